@@ -1,0 +1,325 @@
+"""Pins of the oracle to things other than itself (CPU only).
+
+Each test ties one oracle function to an independent statement of the paper or
+of mathematics:
+
+* cubic root      -- 50-digit mpmath root; the paper's closed form Eq. (root).
+* step_fd         -- dense vector form with the paper's D matrices (Eq. Ddeltax,
+                     Eq. IE-FD-vector-form, numpy.roots); a hand evaluation of
+                     Remark 1's xi with the closed-form root; the collide-and-stream
+                     LB form; the pure-reaction trapezoid flow (lambda = 0); the
+                     linear Fourier growth factor; second-order convergence to the
+                     stationary profile tanh(x / (sqrt 2 eps)).
+* step_lb         -- equal to step_fd to round-off for every d, boundary and omega1.
+* energy          -- dense Phi^T Lambda Phi form; constant fields in closed form;
+                     the exact energy-difference identity Eq. (proof2-eq3).
+* maxnorm         -- NaN propagation and the plain definition on a few values.
+* adjoint_step    -- transpose of the dense Jacobian; central finite differences
+                     of whole runs; checkpointing leaves the result bit-identical.
+* FEX-FD (scheme 1, Remark 2) -- dense explicit formula.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.dense as dense
+
+BCS = [0, 1, 2]
+BCN = {0: "P", 1: "HN", 2: "HD"}
+
+
+def _rand(shape, seed, lo=-1.0, hi=1.0):
+    return np.random.default_rng(seed).uniform(lo, hi, size=shape)
+
+
+# ---------------------------------------------------------------- cubic root
+def test_cubic_root_vs_mpmath(orc):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(11)
+    for dt in (1e-6, 0.0017, 0.0275, 0.2, 1.0, 1.9):
+        for xi in list(rng.uniform(-1.2, 1.2, 40)) + [0.0, 1.0, -1.0, 1e-300, -3.5, 40.0]:
+            a = mp.mpf(dt) / 2
+            p = lambda t: t + a * (t ** 3 - t) - mp.mpf(xi)
+            exact = mp.findroot(p, mp.mpf(xi) / (1 - a))
+            got = orc.cubic_root(dt, xi)
+            assert abs(got - float(exact)) <= 2 * np.spacing(abs(float(exact))) + 1e-320, (dt, xi)
+
+
+def test_cubic_root_vs_paper_closed_form(orc):
+    """Eq. (root): theta0 = (zeta + sqrt(zeta^2 - D^3))^(1/3) + D (zeta + sqrt(...))^(-1/3),
+    zeta = xi/dt, D = (dt - 2)/(3 dt).  Ill-conditioned for small dt, so compared loosely."""
+    rng = np.random.default_rng(5)
+    for dt in (0.01, 0.1, 0.5, 1.0):
+        for xi in rng.uniform(-1, 1, 50):
+            z = xi / dt
+            D = (dt - 2) / (3 * dt)
+            w = (z + math.sqrt(z * z - D ** 3)) ** (1.0 / 3.0)
+            cardano = w + D / w
+            assert orc.cubic_root(dt, xi) == pytest.approx(cardano, abs=1e-11)
+
+
+# ---------------------------------------------------------------- the step
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", [(4,), (7,), (4, 4), (5, 3), (4, 4, 4), (3, 4, 5), (1, 4), (2, 2, 2)])
+def test_step_fd_vs_dense_vector_form(orc, bc, shape):
+    h = 0.1
+    eps = 0.05
+    d = len(shape)
+    dt = 0.9 / (1 + 2 * d * eps * eps / (h * h))
+    phi = _rand(shape, 3 + len(shape) + bc)
+    got = orc.step_fd(phi, eps, dt, h, bc)
+    ref = dense.step(phi, eps, dt, h, bc)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-14)
+
+
+def _hand_point(phi, idx, lam, dt, bc):
+    """Remark 1: xi = (1 - 2 d lam) phi - dt/2 f(phi) + lam sum_k (phi_{i+e_k} + phi_{i-e_k}),
+    ghosts by direct index rules, root by the closed form Eq. (root)."""
+    shape = phi.shape
+    d = len(shape)
+    p = phi[idx]
+    nb = 0.0
+    for k in range(d):
+        for s in (+1, -1):
+            j = list(idx)
+            j[k] += s
+            if 0 <= j[k] < shape[k]:
+                nb += phi[tuple(j)]
+            elif bc == 0:
+                j[k] %= shape[k]
+                nb += phi[tuple(j)]
+            elif bc == 1:
+                nb += p
+    xi = (1 - 2 * d * lam) * p - dt / 2 * (p ** 3 - p) + lam * nb
+    z = xi / dt
+    D = (dt - 2) / (3 * dt)
+    w = (z + math.sqrt(z * z - D ** 3))
+    w = math.copysign(abs(w) ** (1.0 / 3.0), w)
+    return w + D / w
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_step_fd_hand_evaluation_4d(orc, bc, d):
+    shape = (4,) * d
+    phi = _rand(shape, 100 + d * 3 + bc)
+    h, eps, dt = 0.25, 0.1, 0.4
+    lam = eps * eps * dt / (h * h)
+    got = orc.step_fd(phi, eps, dt, h, bc)
+    for idx in np.ndindex(*shape):
+        assert got[idx] == pytest.approx(_hand_point(phi, idx, lam, dt, bc), abs=1e-13)
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("w1_frac", ["1/(2d+1)", "1/(2d)", "0.7/(2d)"])
+def test_lb_form_equals_fd_form(orc, bc, d, w1_frac):
+    """Collide-and-stream (Eqs. fieq-Fi, fneq, RLB, pine) equals Eq. (IE-FD) to round-off."""
+    w1 = {"1/(2d+1)": 1 / (2 * d + 1), "1/(2d)": 1 / (2 * d), "0.7/(2d)": 0.7 / (2 * d)}[w1_frac]
+    shape = {1: (37,), 2: (13, 11), 3: (7, 6, 5)}[d]
+    h = 1.0 / 16
+    eps = 0.02
+    dt = 0.9 * min(1 / (1 + 2 * d * eps * eps / (h * h)), w1 * h * h / (eps * eps))
+    a = _rand(shape, 7 + d + 3 * bc)
+    b = a.copy()
+    for _ in range(50):
+        a = orc.step_lb(a, eps, dt, h, bc, omega1=w1)
+        b = orc.step_fd(b, eps, dt, h, bc)
+    assert np.isfinite(a).all()
+    np.testing.assert_allclose(a, b, rtol=0, atol=5e-14)
+
+
+def test_pure_reaction_is_trapezoid_flow(orc):
+    """lambda = 0: each node follows the trapezoid rule for phi' = phi - phi^3, second order
+    in dt against the exact flow phi0 e^t / sqrt(1 + phi0^2 (e^{2t} - 1))."""
+    phi0 = np.linspace(-0.95, 0.95, 21)
+    T = 1.0
+    errs = []
+    for steps in (50, 100, 200):
+        dt = T / steps
+        phi = orc.run_fd(phi0, 0.0, dt, 1.0, 1, steps)
+        exact = phi0 * math.exp(T) / np.sqrt(1 + phi0 ** 2 * (math.exp(2 * T) - 1))
+        errs.append(np.abs(phi - exact).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.9 < r1 < 4.1 and 3.9 < r2 < 4.1, errs
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_linear_fourier_growth_factor(orc, d):
+    """Periodic, phi = delta cos(2 pi m i / n) along the last axis: the linearized scheme
+    multiplies the mode by g = (1 + a - 4 lam sin^2(pi m / n)) / (1 - a), a = dt/2."""
+    n, m, delta = 16, 3, 1e-9
+    shape = (n,) * d
+    h, eps = 1 / n, 0.03
+    dt = 0.5 / (1 + 2 * d * eps * eps / (h * h))
+    lam = eps * eps * dt / (h * h)
+    i = np.arange(n)
+    mode = delta * np.cos(2 * math.pi * m * i / n)
+    phi = np.broadcast_to(mode, shape).copy()
+    out = orc.step_fd(phi, eps, dt, h, 0)
+    a = dt / 2
+    g = (1 + a - 4 * lam * math.sin(math.pi * m / n) ** 2) / (1 - a)
+    np.testing.assert_allclose(out, g * phi, rtol=1e-12, atol=1e-24)
+
+
+def test_stationary_tanh_second_order(orc):
+    """tanh(x / (sqrt 2 eps)) solves eps^2 phi'' = f(phi); at fixed lambda (dt ~ dx^2) the
+    error after t = 1 on (-1, 1) with Neumann ends converges at order 2."""
+    eps = 0.05
+    lam = 0.2
+    errs = []
+    hs = [1 / 32, 1 / 64, 1 / 128, 1 / 256]
+    for h in hs:
+        N = round(2 / h)
+        x = -1 + h * np.arange(N + 1)
+        prof = np.tanh(x / (math.sqrt(2) * eps))
+        dt = lam * h * h / (eps * eps)
+        steps = round(1.0 / dt)
+        phi = orc.run_fd(prof, eps, 1.0 / steps, h, 1, steps)
+        errs.append(np.abs(phi - prof).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+def test_fex_fd_scheme_vs_dense(orc):
+    """Remark 2's FEX-FD scheme: Phi' = Phi + dt eps^2 Lambda Phi - dt f(Phi)."""
+    for bc in BCS:
+        phi = _rand((5, 4), 40 + bc)
+        h, eps, dt = 0.2, 0.07, 0.3
+        got = orc.step_fd(phi, eps, dt, h, bc, scheme=orc.SCHEME_FEX_FD)
+        L = dense.Lambda_matrix(phi.shape, h, bc)
+        P = phi.reshape(-1)
+        ref = P + dt * eps * eps * (L @ P) - dt * (P ** 3 - P)
+        np.testing.assert_allclose(got.reshape(-1), ref, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_maximum_principle_and_energy_decay(orc, bc, d):
+    """Theorems 2 and 3: with dt <= 1 - 2 d lambda, |phi| <= 1 and E_h never increases."""
+    n = {1: 200, 2: 32, 3: 12}[d]
+    h = 1.0 / n
+    eps = 0.02
+    dt = 0.9 / (1 + 2 * d * eps * eps / (h * h))
+    phi = _rand((n,) * d, 60 + d + bc)
+    E = orc.energy(phi, eps, dt, h, bc)
+    for _ in range(100):
+        phi = orc.step_fd(phi, eps, dt, h, bc)
+        E2 = orc.energy(phi, eps, dt, h, bc)
+        assert E2 <= E + 1e-15 * abs(E)
+        assert orc.maxnorm(phi) <= 1.0
+        E = E2
+
+
+def test_maximum_principle_violated_at_large_dt(orc):
+    """Fig. 3(b): at dt = 1/5 (lambda = 3.28 for m = 8) the maximum principle is lost."""
+    h = 1 / 64
+    eps = 8 * math.tanh(0.9) * h / math.sqrt(2)
+    N = round(3 / h)
+    x = -0.5 + h * np.arange(N + 1)
+    phi = 0.5 * (1 - np.tanh(x / (2 * math.sqrt(2) * eps)))
+    worst = 0.0
+    for _ in range(20):
+        phi = orc.step_fd(phi, eps, 0.2, h, 1)
+        worst = max(worst, orc.maxnorm(phi))
+    assert worst > 1.0
+
+
+# ---------------------------------------------------------------- energy
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", [(6,), (4, 5), (3, 4, 4)])
+def test_energy_vs_dense(orc, bc, shape):
+    phi = _rand(shape, 80 + bc + len(shape))
+    h, eps, dt = 0.1, 0.04, 0.05
+    assert orc.energy(phi, eps, dt, h, bc) == pytest.approx(dense.energy(phi, eps, dt, h, bc),
+                                                              rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_energy_constant_fields(orc, d):
+    n, h, eps, dt = 6, 0.1, 0.3, 0.01
+    one = np.ones((n,) * d)
+    for bc in (0, 1):
+        assert orc.energy(one, eps, dt, h, bc) == 0.0
+        assert orc.energy(-one, eps, dt, h, bc) == 0.0
+    c = 0.5
+    # Dirichlet: bulk n^d (c^2-1)^2/4 plus 2 d n^(d-1) boundary links of (c - 0)^2 / h^2
+    exact = h ** d * (n ** d * (c * c - 1) ** 2 / 4 + eps * eps / 2 * 2 * d * n ** (d - 1) * c * c / (h * h))
+    assert orc.energy(c * one, eps, dt, h, 2) == pytest.approx(exact, rel=1e-14)
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", [(9,), (4, 5), (3, 3, 4)])
+def test_energy_difference_identity(orc, bc, shape):
+    """Eq. (proof2-eq3), an exact identity of the scheme:
+    E' - E = -dx^d/4 sum (p'^3 + p^3 - p' p^2 - p'^2 p)(p' - p) - dx^d/dt sum (p' - p)^2
+             - dx^d lam/(2 dt) (P' - P)^T Lambda (P' - P),  Lambda = dx^2 Lambda_dx."""
+    h, eps = 0.1, 0.05
+    d = len(shape)
+    dt = 0.8 / (1 + 2 * d * eps * eps / (h * h))
+    lam = eps * eps * dt / (h * h)
+    p = _rand(shape, 90 + bc + d)
+    q = orc.step_fd(p, eps, dt, h, bc)
+    dE = orc.energy(q, eps, dt, h, bc) - orc.energy(p, eps, dt, h, bc)
+    P, Q = p.reshape(-1), q.reshape(-1)
+    dl = Q - P
+    Lam = h * h * dense.Lambda_matrix(shape, h, bc)
+    rhs = (-h ** d / 4 * np.sum((Q ** 3 + P ** 3 - Q * P * P - Q * Q * P) * dl)
+           - h ** d / dt * np.sum(dl * dl) - h ** d * lam / (2 * dt) * (dl @ Lam @ dl))
+    assert dE == pytest.approx(rhs, rel=1e-9, abs=1e-15)
+    assert dE <= 0
+
+
+def test_maxnorm(orc):
+    assert orc.maxnorm(np.array([0.5, -0.75, 0.25])) == 0.75
+    assert orc.maxnorm(np.array([[0.0, 1.0], [-1.0, 0.5]])) == 1.0
+    v = np.array([0.1, np.nan, 0.2])
+    assert math.isnan(orc.maxnorm(v))
+
+
+# ---------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", [(7,), (4, 5), (3, 4, 3), (2,), (1, 3)])
+def test_adjoint_step_is_jacobian_transpose(orc, bc, shape):
+    h, eps = 0.1, 0.05
+    d = len(shape)
+    dt = 0.8 / (1 + 2 * d * eps * eps / (h * h))
+    p = _rand(shape, 200 + bc + d)
+    q = orc.step_fd(p, eps, dt, h, bc)
+    w = _rand(shape, 300 + bc + d)
+    adj, ge = orc.adjoint_step(p, q, w, eps, dt, h, bc)
+    J = dense.jacobian(p, q, eps, dt, h, bc)
+    np.testing.assert_allclose(adj.reshape(-1), J.T @ w.reshape(-1), rtol=1e-12, atol=1e-14)
+    de = dense.d_step_d_eps2(p, q, dt, h, bc)
+    assert ge == pytest.approx(float(de @ w.reshape(-1)), rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+def test_grad_vs_central_differences(orc, bc):
+    shape = (6, 5)
+    h, eps = 1 / 6, 0.08
+    dt = 0.8 / (1 + 4 * eps * eps / (h * h))
+    steps = 12
+    phi0 = _rand(shape, 400 + bc, -0.6, 0.6)
+    target = _rand(shape, 500 + bc)
+
+    def loss(p0, e):
+        pT = orc.run_fd(p0, e, dt, h, bc, steps)
+        return float(np.mean((pT - target) ** 2))
+
+    pT = orc.run_fd(phi0, eps, dt, h, bc, steps)
+    gT = 2 * (pT - target) / pT.size
+    g0, ge2 = orc.grad(phi0, eps, dt, h, bc, steps, gT, checkpoint_every=5)
+    v = _rand(shape, 600 + bc)
+    s = 1e-6
+    fd = (loss(phi0 + s * v, eps) - loss(phi0 - s * v, eps)) / (2 * s)
+    assert float(np.sum(g0 * v)) == pytest.approx(fd, rel=1e-6)
+    # d/d(eps^2) with dt, dx fixed: perturb eps^2 and take the square root
+    se = 1e-7
+    fde = (loss(phi0, math.sqrt(eps * eps + se)) - loss(phi0, math.sqrt(eps * eps - se))) / (2 * se)
+    assert ge2 == pytest.approx(fde, rel=1e-5)
+    g0b, ge2b = orc.grad(phi0, eps, dt, h, bc, steps, gT, checkpoint_every=0)
+    assert np.array_equal(g0, g0b) and ge2 == ge2b
