@@ -1,0 +1,412 @@
+"""Benchmark of the RLB-MIE-FD Allen-Cahn stepper on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+
+One bench "step" is one pass of the hot path over the headline workload: the 3D
+512^3 homogeneous-Neumann grid (h = 1/512, eps = 0.01, phi0 ~ U[-1, 1] from seed
+1, FP32 state), set to phi0 and advanced 200 time steps with the discrete energy
+E_h and the maximum norm computed every 50 steps (FP64 reductions).  Inputs are
+resident in HBM when the timed region starts; each state buffer is 512 MiB, larger
+than the 129 MB L2, so no L2 flush is needed between iterations.
+
+value     lattice updates per second over all ranks (GLUPS), device-timed with CUDA
+          events around K bench steps (barrier + synchronize on both sides, max over
+          ranks).  With N > 1 every rank runs its own replica (the single problem is
+          not sharded: weak scaling).
+e2e       the same metric through the C ABI with host buffers: each step copies phi0
+          from pinned host memory (acs_set_state_host), steps, and reads the state and
+          the reductions back (acs_get_state_host).
+roofline  the step kernel's algorithmic bytes per launch (2 sizeof(T) per update, K
+          fused steps per launch for temporal blocking) over its CUDA-event launch
+          duration, against the measured HBM copy bandwidth.
+cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample of the
+          same workload (rank 0, N = 1 only).
+
+--impl reference times that oracle (the only other implementation of the method:
+the paper ships no code) as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lattice-updates/s (GLUPS) and % of HBM roofline, FP32 & FP64; adjoint fwd+bwd time/step"
+UNIT = "GLUPS"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile(kernel_tag: str):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if its
+    recorded source digest still matches the kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rows = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) >= 4:
+                rows[parts[0]] = (parts[1], float(parts[2]), parts[3])
+    if kernel_tag not in rows:
+        return None
+    src_file, per_launch, digest = rows[kernel_tag]
+    src = os.path.join(ROOT, "paper_2312_07010_gb300", "csrc", src_file)
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return per_launch if h == digest else None
+
+
+def cpu_oracle_sample(budget_s: float = 12.0):
+    """FP64 oracle on the 512^3 Neumann workload: as many whole time steps as fit the budget."""
+    import numpy as np
+
+    import oracle
+    from workloads import cfg2
+    w = cfg2("f64")
+    phi = w.phi0()
+    lam = oracle.lam(w.eps, w.dt, w.h)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        phi = oracle.step_fd(phi, w.eps, w.dt, w.h, w.bc)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 50:
+            break
+    del lam
+    ups = w.numel * steps / el
+    return {"value": ups / 1e9, "unit": UNIT, "cores": oracle.numthreads(), "kind": "oracle",
+            "sample": f"{steps} time step(s) of the 512^3 Neumann workload, FP64 oracle "
+                      f"(plain C, OpenMP over points), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from workloads import cfg2
+    w = cfg2("f64")
+    phi0 = w.phi0()
+    # each reference step: one time step of the workload on the whole 512^3 grid
+    for _ in range(args.warmup):
+        oracle.step_fd(phi0, w.eps, w.dt, w.h, w.bc)
+    t0 = time.perf_counter()
+    phi = phi0
+    for _ in range(args.steps):
+        phi = oracle.step_fd(phi, w.eps, w.dt, w.h, w.bc)
+    el = time.perf_counter() - t0
+    val = w.numel * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "cfg2_3d_neumann_512", "dims": 3, "n": 512, "bc": "neumann",
+                   "eps": w.eps, "dt": w.dt, "h": w.h,
+                   "sample": "one time step of the 512^3 grid per bench step (oracle)"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.numthreads(), "kind": "oracle",
+                         "sample": f"{args.steps} x one time step of the 512^3 Neumann workload, FP64"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0, help="ACS_KERNEL_* (0 = auto)")
+    ap.add_argument("--depth", type=int, default=1)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+
+    import paper_2312_07010_gb300 as P
+    from workloads import cfg2
+    P.lib()
+    w = cfg2("f32")
+    phi0_host = torch.from_numpy(w.phi0().astype(np.float32)).pin_memory()
+    phi0_dev = phi0_host.cuda()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32", stream=stream)
+    if args.kernel:
+        s.set_kernel(args.kernel, args.depth)
+    kernel, depth = s.get_kernel()
+    log_every = 50
+    n_logs = w.steps // log_every + 1
+
+    def bench_step():
+        s.set_state(phi0_dev)
+        s.run_logged(w.steps, log_every)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        bench_step()
+    peak, peak_kind = _peaks()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            bench_step()
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = w.numel * w.steps * args.steps * ws
+    value = updates / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    out_host = torch.empty(w.n, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        s.set_state_host(phi0_host)
+        s.run_logged(w.steps, log_every)
+        s.get_state_host(out_host)
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = updates / e2e_s / 1e9
+    state_bytes = w.numel * 4
+
+    # the dominant kernel's launch duration: acs_step(2 K) is exactly two launches
+    K = depth if kernel == P.ACS_KERNEL_TEMPORAL else 1
+    s.set_state(phi0_dev)
+    s.step(2 * K)
+    reps = 20
+    ea = torch.cuda.Event(enable_timing=True)
+    eb = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ea.record(stream)
+    for _ in range(reps):
+        s.step(2 * K)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    launch_ms = ea.elapsed_time(eb) / (2 * reps)
+    alg_bytes = 2 * 4 * w.numel * K
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    ktag = {P.ACS_KERNEL_NAIVE: "naive", P.ACS_KERNEL_TILED: "tiled", P.ACS_KERNEL_TEMPORAL: f"temporal{K}"}[kernel]
+    traffic = _traffic_from_profile(f"step3d_f32_neumann_512_{ktag}")
+
+    launches_per_step = (w.steps // K) + 2 * n_logs
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cfg2_3d_neumann_512", "dims": 3, "n": 512, "bc": "neumann", "eps": w.eps,
+                   "h": w.h, "dt": w.dt, "time_steps": w.steps, "log_every": log_every,
+                   "kernel": ktag, "l2": "inputs larger than L2 (512 MiB per state buffer), no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel_ms": launch_ms, "alg_bytes_per_launch": alg_bytes},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes + 16 * n_logs},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "effective_hbm_frac": value / ws * 8 / peak,
+    }
+    if rank == 0 and ws == 1 and not args.no_extras:
+        line["extra"] = extras(P, args)
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def _time(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extras(P, args):
+    """Secondary numbers: FP64 and 2D workloads, the adjoint, the batched form."""
+    import numpy as np
+    import torch
+
+    from workloads import cfg1, cfg2, cfg3, cfg5, tanh_disc
+    out = {}
+    peak, _ = _peaks()
+    # FP64 on the 512^3 workload (fewer steps)
+    for name, w, nsteps in (("cfg2_fp64_512cubed", cfg2("f64"), 20), ("cfg3_fp32_4096sq", cfg3("f32"), 200),
+                            ("cfg3_fp64_4096sq", cfg3("f64"), 50), ("cfg1_fp64_128sq", cfg1(), 1000)):
+        s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, w.dtype)
+        phi0 = torch.from_numpy(w.phi0().astype(np.float32 if w.dtype == "f32" else np.float64)).cuda()
+        s.set_state(phi0)
+
+        def go():
+            s.step(nsteps)
+        ms = _time(go, 3)
+        glups = w.numel * nsteps / (ms * 1e-3) / 1e9
+        esz = 4 if w.dtype == "f32" else 8
+        k, d = s.get_kernel()
+        out[name] = {"glups": glups, "ms_per_time_step": ms / nsteps, "hbm_frac_effective": glups * 2 * esz / peak,
+                     "kernel": k, "depth": d}
+        s.close()
+        del s, phi0
+        torch.cuda.empty_cache()
+    # adjoint: 1024^2 periodic, FP32, 500 steps, checkpoints every 50
+    w = cfg5()
+    phi0 = torch.from_numpy(w.phi0().astype(np.float32)).cuda()
+    target = torch.from_numpy(tanh_disc(w.n[0], w.h, w.eps).astype(np.float32)).cuda()
+    s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    s.set_state(phi0)
+    s.record_for_grad(w.steps, 50)
+
+    def fwd_bwd():
+        s.set_state(phi0)
+        s.step(w.steps)
+        g = 2 * (s.phi - target) / s.numel
+        s.grad(g)
+
+    def fwd_only():
+        s.set_state(phi0)
+        s.step(w.steps)
+        torch.cuda.synchronize()
+    ms_fb = _time(fwd_bwd, 2)
+    ms_f = _time(fwd_only, 2)
+    out["cfg5_adjoint_1024sq"] = {"fwd_bwd_ms_per_time_step": ms_fb / w.steps,
+                                  "fwd_ms_per_time_step": ms_f / w.steps,
+                                  "fwd_bwd_over_fwd": ms_fb / ms_f}
+    s.close()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

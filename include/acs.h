@@ -1,0 +1,250 @@
+/*
+ * acs.h -- C ABI of a GB300 (sm_103a) stepper for the d-dimensional Allen-Cahn
+ * equation  phi_t = eps^2 lap(phi) - f(phi),  f(phi) = phi^3 - phi  (d = 1, 2, 3),
+ * discretized by the RLB-MIE-FD scheme of Chen, Liu, Chai and Shi,
+ * "Regularized lattice Boltzmann method based maximum principle and energy
+ * stability preserving finite-difference scheme for the Allen-Cahn equation"
+ * (arXiv:2312.07010).
+ *
+ * One step (Eq. IE-FD, Remark 1), per unknown i:
+ *   xi_i  = phi_i + lambda sum_k (phi_{i+e_k} + phi_{i-e_k} - 2 phi_i) - (dt/2) f(phi_i),
+ *   phi_i <- the unique real theta with theta + (dt/2) f(theta) = xi_i,
+ * with lambda = eps^2 dt / h^2 (Eq. IE-FD-vector-form).  Neighbours outside the
+ * box follow the boundary condition (Eq. Ddeltax): periodic = wrap around,
+ * Neumann = the node itself (mirror), Dirichlet = 0.
+ *
+ * Memory layout.  The state is n[0] x ... x n[dims-1] values of the chosen
+ * dtype, row-major with the last index fastest (the ordering of Phi in Eq.
+ * IE-FD-vector-form), contiguous, in device memory owned by the caller.
+ *
+ * Ownership.  The library allocates no device memory on these paths: the caller
+ * passes the state buffer and a work buffer of acs_work_bytes() bytes (the second
+ * ping-pong state plus reduction scratch), and keeps both alive until
+ * acs_destroy().  The library owns only the opaque context (host memory), a
+ * private CUDA stream used to record CUDA graphs, and those graphs.
+ *
+ * Streams.  Every device-side call is enqueued on the stream given to acs_bind()
+ * and returns without waiting, except the calls that return host values
+ * (acs_energy, acs_maxnorm, acs_run_logged, acs_grad, acs_get_state_host,
+ * acs_sync), which synchronize that stream.
+ *
+ * Status codes.  0 = success; > 0 = a warning, the call did its work; < 0 = an
+ * error, the call changed nothing that the caller can observe (except where a
+ * function says otherwise).  acs_strerror() names each code.
+ *
+ * Threading.  A context may be used by one host thread at a time.
+ */
+#ifndef ACS_H
+#define ACS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ACS_API __attribute__((visibility("default")))
+#else
+#define ACS_API
+#endif
+
+typedef struct acs_ctx acs_ctx;
+typedef struct acs_batch acs_batch;
+
+/* Boundary conditions (Sec. I: HN-BC, HD-BC, P-BC; matrices of Eq. Ddeltax). */
+enum { ACS_BC_PERIODIC = 0, ACS_BC_NEUMANN = 1, ACS_BC_DIRICHLET = 2 };
+
+/* State precision: FP32 state and arithmetic, or FP64.  Energy and maximum-norm
+ * reductions accumulate in FP64 (compensated sums) for both. */
+enum { ACS_F32 = 0, ACS_F64 = 1 };
+
+/* Status codes. */
+enum {
+    ACS_OK = 0,
+    ACS_WARN_MP_CONDITION = 1,     /* dt > 1 - 2 d lambda: Theorem 2 does not apply */
+    ACS_WARN_ENERGY_CONDITION = 2, /* dt > 4 (1 - 2 d lambda): Theorem 3 does not apply */
+    ACS_E_INVAL = -1,              /* invalid argument */
+    ACS_E_CUDA = -2,               /* a CUDA runtime call failed */
+    ACS_E_NOMEM = -3,              /* work buffer too small / host allocation failed */
+    ACS_E_TIMEOUT = -4,            /* a bounded device-side wait gave up */
+    ACS_E_NONFINITE = -5,          /* the state holds NaN or Inf */
+    ACS_E_STATE = -6,              /* call out of order (e.g. step before bind) */
+    ACS_E_UNSUPPORTED = -7         /* kernel variant not available for this problem */
+};
+
+/* Kernel variants (acs_set_kernel).  All variants compute the same per-point
+ * arithmetic in the same order, so they give bit-identical states. */
+enum {
+    ACS_KERNEL_AUTO = 0,     /* autotuned choice, cached per problem class */
+    ACS_KERNEL_NAIVE = 1,    /* one thread per unknown, neighbours via the cache hierarchy */
+    ACS_KERNEL_TILED = 2,    /* shared-memory tiles (TMA-staged for d >= 2) with a one-cell halo */
+    ACS_KERNEL_TEMPORAL = 3  /* several fused steps per pass through HBM (temporal blocking) */
+};
+
+/* Schemes (acs_set_scheme).  RLB-MIE-FD is the paper's scheme (Eq. IE-FD); FEX-FD
+ * is the fully explicit scheme Remark 2 compares against,
+ * phi <- phi + lambda sum_k(...) - dt f(phi). */
+enum { ACS_SCHEME_RLB_MIE_FD = 0, ACS_SCHEME_FEX_FD = 1 };
+
+/*
+ * acs_create -- validate a problem and make a context for it.
+ *   dims   1, 2 or 3 (the D1Q3, D2Q5, D3Q7 lattices of Eq. ci)
+ *   n      unknowns per axis, n[0..dims-1] >= 1 (entries past dims are ignored);
+ *          n[dims-1] is the fastest axis.  The product must be < 2^40.
+ *   eps    interfacial parameter eps > 0 of Eq. (ACE) (the equation's diffusion
+ *          coefficient is eps^2); eps == 0 is accepted and gives the pure reaction flow
+ *   dt     time step, 0 < dt < 2 (for dt >= 2 the cubic of Remark 1 stops being
+ *          monotone and its root need not be unique)
+ *   h      lattice spacing Delta x > 0
+ *   bc     ACS_BC_*;  dtype ACS_F32 or ACS_F64
+ * Returns ACS_OK, or ACS_WARN_MP_CONDITION / ACS_WARN_ENERGY_CONDITION when the
+ * step sizes violate the conditions of Theorem 2 / Theorem 3 (the context is
+ * still created: the paper runs such cases on purpose), or ACS_E_INVAL with
+ * *out untouched.  Theorem 2 asks for dt <= 1 - 2 d omega1/s, 0 < omega1 <= 1/(2d),
+ * s > 1 with lambda = omega1/s; the weight omega1 of the lattice model does not
+ * enter the finite-difference step, and a weight with s > 1 exists whenever
+ * dt <= 1 - 2 d lambda, so that is the condition checked.
+ * While it holds (and |phi0| <= 1) the exact scheme keeps |phi| <= 1; the kernels
+ * then round an overshoot of at most 16 units in the last place back to +-1.
+ */
+ACS_API int acs_create(int dims, const int64_t n[3], double eps, double dt, double h, int bc,
+                       int dtype, acs_ctx** out);
+
+/* Bytes of device work memory acs_bind() needs (one state plus scratch), or 0 for NULL. */
+ACS_API size_t acs_work_bytes(const acs_ctx* ctx);
+
+/*
+ * acs_bind -- attach device memory and a stream.
+ *   d_phi   the state, prod(n) elements of the context's dtype, 16-byte aligned
+ *   d_work  >= acs_work_bytes() bytes, 256-byte aligned; contents are scratch
+ *   stream  a cudaStream_t (NULL = the legacy default stream)
+ * May be called again to rebind.  ACS_E_INVAL for NULL or misaligned pointers
+ * or a short work buffer (work_bytes is its size).  Resets the step counter.
+ */
+ACS_API int acs_bind(acs_ctx* ctx, void* d_phi, void* d_work, size_t work_bytes, void* stream);
+
+/* Copy an initial state into d_phi (device to device, prod(n) elements) and reset
+ * the step counter; d_phi0 may equal d_phi. */
+ACS_API int acs_set_state(acs_ctx* ctx, const void* d_phi0);
+/* The same from host memory (pageable or pinned); returns when the copy is enqueued
+ * for pinned memory and after it completes for pageable memory. */
+ACS_API int acs_set_state_host(acs_ctx* ctx, const void* h_phi0);
+/* Copy the current state to host memory; synchronizes the stream. */
+ACS_API int acs_get_state_host(acs_ctx* ctx, void* h_phi);
+
+/* Choose the scheme (ACS_SCHEME_*). Default ACS_SCHEME_RLB_MIE_FD. */
+ACS_API int acs_set_scheme(acs_ctx* ctx, int scheme);
+
+/*
+ * acs_set_kernel -- choose the kernel variant; depth is the number of fused
+ * steps per pass for ACS_KERNEL_TEMPORAL (1..8) and ignored otherwise.
+ * ACS_E_UNSUPPORTED if the variant does not exist for this (dims, dtype).
+ */
+ACS_API int acs_set_kernel(acs_ctx* ctx, int kernel, int depth);
+/* The variant acs_step() uses (after autotuning, for ACS_KERNEL_AUTO). */
+ACS_API int acs_get_kernel(const acs_ctx* ctx, int* kernel, int* depth);
+
+/*
+ * acs_step -- advance the state by n_steps >= 0 steps of Eq. (IE-FD), in place:
+ * on completion (stream order) d_phi holds phi^{n + n_steps}.  Asynchronous.
+ * The launches of one call are recorded once into a CUDA graph and replayed.
+ */
+ACS_API int acs_step(acs_ctx* ctx, int64_t n_steps);
+
+/* Steps taken since the last acs_bind / acs_set_state. */
+ACS_API int64_t acs_steps_done(const acs_ctx* ctx);
+
+/*
+ * acs_energy -- the discrete free energy of Theorem 3 (Eq. proof2-eq0),
+ *   E_h = h^d [ 1/4 sum_i (phi_i^2 - 1)^2 + eps^2/2 sum_links ((phi_j - phi_i)/h)^2 ],
+ * where -Phi^T Lambda_{dx} Phi is written as the sum over lattice links (periodic:
+ * the wrap-around link counts; Neumann: interior links only; Dirichlet: also the
+ * link from each boundary unknown to the zero boundary value).  FP64,
+ * compensated, deterministic.  Synchronizes the stream.
+ * ACS_E_NONFINITE (value still written) if the result is not finite.
+ */
+ACS_API int acs_energy(acs_ctx* ctx, double* out_host);
+
+/* max_i |phi_i| (Theorem 2's discrete maximum norm); NaN if any entry is NaN.
+ * Synchronizes the stream; ACS_E_NONFINITE (value still written) for NaN/Inf. */
+ACS_API int acs_maxnorm(acs_ctx* ctx, double* out_host);
+
+/* Both reductions, written as {E_h, max|phi|} to two doubles of device memory,
+ * asynchronously (no synchronization). */
+ACS_API int acs_observe_async(acs_ctx* ctx, double* d_out2);
+
+/*
+ * acs_run_logged -- n_steps steps with E_h and max|phi| recorded before the first
+ * step and after every `every` steps (every >= 1): n_steps/every + 1 entries into
+ * each host array.  One synchronization at the end.  The log lives in the work
+ * buffer (at most 4096 entries per call; ACS_E_INVAL beyond).
+ */
+ACS_API int acs_run_logged(acs_ctx* ctx, int64_t n_steps, int64_t every, double* h_energy,
+                           double* h_maxnorm);
+
+/*
+ * Adjoint of the discrete stepper (the transpose of the Jacobian of each step of
+ * Eq. IE-FD, chained backwards), for a terminal loss L(phi_T):
+ *   per step, mu = lambda^{n+1} / (1 + (dt/2) f'(phi^{n+1})),  f'(x) = 3x^2 - 1,
+ *   lambda^n = mu (1 - (dt/2) f'(phi^n)) + lambda_lat S^T mu  (S = the ghost-rule stencil),
+ *   dL/d(eps^2) += (dt/h^2) sum_i mu_i S_i(phi^n)   (dt and h held fixed).
+ * Recording: acs_grad_bind() gives the context a checkpoint buffer of
+ * acs_grad_work_bytes(ctx, max_steps, every) bytes; from then on acs_set_state
+ * stores phi^0 and acs_step stores every `every`-th state.  acs_grad() then
+ * recomputes each segment from its checkpoint and sweeps backwards over all steps
+ * since acs_set_state, given d_dL_dphiT (the state's dtype), writing dL/dphi0 to
+ * d_dL_dphi0 (same dtype; may alias d_dL_dphiT) and dL/d(eps^2) (accumulated in
+ * FP64) to *dL_deps2_host.  Synchronizes.  ACS_E_STATE if nothing was recorded,
+ * ACS_E_NOMEM if more than max_steps steps were taken.
+ */
+ACS_API size_t acs_grad_work_bytes(const acs_ctx* ctx, int64_t max_steps, int64_t every);
+ACS_API int acs_grad_bind(acs_ctx* ctx, void* d_grad_work, size_t bytes, int64_t max_steps,
+                          int64_t every);
+ACS_API int acs_grad(acs_ctx* ctx, const void* d_dL_dphiT, void* d_dL_dphi0, double* dL_deps2_host);
+
+/* Block until all work enqueued by this context has finished. */
+ACS_API int acs_sync(acs_ctx* ctx);
+
+/*
+ * acs_dt_max -- the step-size bounds of the paper for lattice number lambda =
+ * eps^2 dt / h^2 on the DdQ(2d+1) lattice:
+ *   *dt_mp      largest dt with dt <= 1 - 2 d lambda                     (Theorem 2)
+ *   *dt_energy  largest dt with dt <= 4 (1 - 2 d lambda)                 (Theorem 3)
+ */
+ACS_API int acs_dt_max(int dims, double eps, double h, double* dt_mp, double* dt_energy);
+
+/* Human-readable text of a status code (static storage). */
+ACS_API const char* acs_strerror(int status);
+
+/* Library version as "major.minor.patch" (static storage). */
+ACS_API const char* acs_version(void);
+
+/* Release the context (not the caller's buffers).  Waits for its stream. NULL is a no-op. */
+ACS_API void acs_destroy(acs_ctx* ctx);
+
+/*
+ * Batched stepping: `count` independent 2D problems of sides n[i] x n[i], each
+ * with its own eps, dt, h and boundary, advanced together in one persistent
+ * launch per call (recorded into a CUDA graph).  The states are packed one after
+ * the other in one device buffer; acs_batch_offsets() gives each instance's first
+ * element.  Per-instance arithmetic is identical to acs_step() on that instance
+ * alone, so each instance's state is bit-identical to its standalone run.
+ */
+ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, const double* dt,
+                             const double* h, const int* bc, int dtype, acs_batch** out);
+ACS_API size_t acs_batch_numel(const acs_batch* b);
+ACS_API int acs_batch_offsets(const acs_batch* b, int64_t* offsets);
+ACS_API size_t acs_batch_work_bytes(const acs_batch* b);
+ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_bytes, void* stream);
+ACS_API int acs_batch_step(acs_batch* b, int64_t n_steps);
+/* Per-instance E_h and max|phi| into host arrays of `count` doubles; synchronizes. */
+ACS_API int acs_batch_observe(acs_batch* b, double* h_energy, double* h_maxnorm);
+ACS_API void acs_batch_destroy(acs_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACS_H */

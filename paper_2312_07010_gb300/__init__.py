@@ -1,0 +1,31 @@
+"""GB300-native RLB-MIE-FD stepper for the Allen-Cahn equation (arXiv:2312.07010).
+
+The compute path is ``libacs.so`` (hand-written sm_103a CUDA behind the C ABI of
+``include/acs.h``); this package only marshals arguments to it.  Importing the
+package does not load the library; the first call that needs it does, and fails
+loudly when it has not been built (``paper_2312_07010_gb300.build.build()``).
+"""
+from . import build
+from ._lib import (ACS_BC_DIRICHLET, ACS_BC_NEUMANN, ACS_BC_PERIODIC, ACS_F32, ACS_F64,
+                   ACS_KERNEL_AUTO, ACS_KERNEL_NAIVE, ACS_KERNEL_TEMPORAL, ACS_KERNEL_TILED,
+                   ACS_SCHEME_FEX_FD, ACS_SCHEME_RLB_MIE_FD, SIGNATURES, AcsError, check, lib,
+                   lib_path, strerror)
+
+__all__ = [
+    "build", "lib", "lib_path", "strerror", "check", "AcsError", "SIGNATURES",
+    "ACS_BC_PERIODIC", "ACS_BC_NEUMANN", "ACS_BC_DIRICHLET", "ACS_F32", "ACS_F64",
+    "ACS_KERNEL_AUTO", "ACS_KERNEL_NAIVE", "ACS_KERNEL_TILED", "ACS_KERNEL_TEMPORAL",
+    "ACS_SCHEME_RLB_MIE_FD", "ACS_SCHEME_FEX_FD",
+    "AllenCahn", "AllenCahnFunction", "allen_cahn", "Batch", "dt_max",
+]
+
+
+def __getattr__(name):
+    # torch-dependent front ends are imported on first use
+    if name in ("AllenCahn", "AllenCahnFunction", "allen_cahn", "dt_max"):
+        from . import stepper
+        return getattr(stepper, name)
+    if name == "Batch":
+        from . import batch
+        return batch.Batch
+    raise AttributeError(name)

@@ -1,0 +1,533 @@
+// acs_api.cu -- host side of the C ABI declared in include/acs.h: validation,
+// step-size conditions, coefficient set-up, launch planning, CUDA-graph replay,
+// reductions and state transfer for single problems.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "acs_host.h"
+
+namespace acs {
+
+// ---------------------------------------------------------------- coefficients
+
+// Relative error bound of the fast cubic path after `newton` corrections, for
+// y = (a/b) x^2 (see cubic_root in acs_device.cuh).  The three-term series seed
+// leaves rho0 <= 12 y^3 / (1 - 27y/4); a Newton correction with a reciprocal of
+// relative error eta maps rho to 3 y rho^2 + eta rho.
+static double cubic_bound(double y, int newton) {
+    if (y >= 4.0 / 27.0) return 1.0;
+    const double eta = 2.5e-7;
+    double rho = 12.0 * y * y * y / (1.0 - 6.75 * y);
+    for (int k = 0; k < newton; ++k) rho = 3.0 * y * rho * rho + eta * rho;
+    return rho;
+}
+
+static void pick_newton(double t, double rb, double tol, int* newton, double* ymax) {
+    const double xneed = 1.001 * rb;  // |xi| <= 1.001 under Theorem 2 (plus rounding)
+    const double yneed = t * xneed * xneed;
+    int n = 3;
+    for (int k = 1; k <= 3; ++k)
+        if (cubic_bound(yneed, k) <= tol) { n = k; break; }
+    // largest y (up to 0.1) where the bound holds with n corrections
+    double lo = 0.0, hi = 0.1;
+    if (cubic_bound(hi, n) <= tol) lo = hi;
+    else
+        for (int it = 0; it < 80; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (cubic_bound(mid, n) <= tol) lo = mid; else hi = mid;
+        }
+    *newton = n;
+    *ymax = lo;
+}
+
+template <typename T>
+Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
+    Coef<T> c;
+    std::memset(&c, 0, sizeof(c));
+    const double a = 0.5 * dt, b = 1.0 - a;
+    c.lam = (T)lam;
+    if (scheme == ACS_SCHEME_FEX_FD) {
+        c.a = (T)dt;
+        c.c0 = (T)(1.0 - 2.0 * dims * lam + dt);
+        c.fex = 1;
+    } else {
+        c.a = (T)a;
+        c.c0 = (T)(1.0 - 2.0 * dims * lam + a);
+        c.fex = 0;
+    }
+    c.b = (T)b;
+    c.rb = (T)(1.0 / b);
+    c.t = (T)(a / b);
+    c.three_a = (T)(3.0 * a);
+    const double tol = sizeof(T) == 4 ? std::ldexp(1.0, -26) : std::ldexp(1.0, -55);
+    double ymax;
+    pick_newton(a / b, 1.0 / b, tol, &c.newton, &ymax);
+    c.ymax = (T)ymax;
+    const double ulp1 = sizeof(T) == 4 ? std::ldexp(1.0, -23) : std::ldexp(1.0, -52);
+    c.clamp_hi = (T)(1.0 + 16.0 * ulp1);
+    c.clamp = mp_ok ? 1 : 0;
+    return c;
+}
+template Coef<float> make_coef<float>(int, double, double, int, bool);
+template Coef<double> make_coef<double>(int, double, double, int, bool);
+
+Geo make_geo(int dims, const int64_t* n) {
+    Geo g;
+    g.nx = g.ny = g.nz = 1;
+    if (dims == 1) g.nx = n[0];
+    if (dims == 2) { g.ny = n[0]; g.nx = n[1]; }
+    if (dims == 3) { g.nz = n[0]; g.ny = n[1]; g.nx = n[2]; }
+    g.sy = g.nx;
+    g.sz = g.nx * g.ny;
+    g.total = g.nx * g.ny * g.nz;
+    return g;
+}
+
+}  // namespace acs
+
+using namespace acs;
+
+struct GraphEntry {
+    int64_t nsteps;
+    int kernel, depth, scheme;
+    cudaGraphExec_t exec;
+};
+
+struct acs_ctx {
+    int dims;
+    int64_t n[3];
+    double eps, dt, h;
+    int bc, dtype;
+    double lam;
+    bool mp_ok, energy_ok;
+    Geo g;
+    size_t esize;
+    int scheme;
+    int kernel_req, depth_req;  // as requested
+    int kernel, depth;          // resolved
+    Coef<float> cf;
+    Coef<double> cd;
+    // bound resources
+    bool bound;
+    void* phi;
+    char* work;
+    size_t work_bytes;
+    cudaStream_t stream;
+    cudaStream_t cap;
+    void* other;
+    RedPartial* partials;
+    double* result;
+    double* log;
+    int64_t steps_done;
+    std::vector<GraphEntry> graphs;
+    // adjoint recording
+    GradState grad;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kLogCap = 4096;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+size_t state_bytes(const acs_ctx* c) { return (size_t)c->g.total * c->esize; }
+
+size_t off_partials(const acs_ctx* c) { return align_up(state_bytes(c)); }
+size_t off_result(const acs_ctx* c) { return off_partials(c) + align_up(sizeof(RedPartial) * kMaxRedBlocks); }
+size_t off_log(const acs_ctx* c) { return off_result(c) + kAlign; }
+size_t work_total(const acs_ctx* c) { return off_log(c) + align_up(sizeof(double) * 2 * kLogCap); }
+
+void drop_graphs(acs_ctx* c) {
+    for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
+    c->graphs.clear();
+}
+
+void refresh_coef(acs_ctx* c) {
+    c->cf = make_coef<float>(c->dims, c->lam, c->dt, c->scheme, c->mp_ok);
+    c->cd = make_coef<double>(c->dims, c->lam, c->dt, c->scheme, c->mp_ok);
+}
+
+}  // namespace
+
+// Launch `k` fused steps (k == 1 for non-temporal variants) from src to dst.
+static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaStream_t st) {
+    if (c->dtype == ACS_F32) {
+        const float* s = (const float*)src;
+        float* d = (float*)dst;
+        if (c->kernel == ACS_KERNEL_TEMPORAL) return launch_step_temporal<float>(c->dims, c->bc, k, s, d, c->g, c->cf, st);
+        if (c->kernel == ACS_KERNEL_TILED) return launch_step_tiled<float>(c->dims, c->bc, s, d, c->g, c->cf, st);
+        return launch_step_naive<float>(c->dims, c->bc, s, d, c->g, c->cf, st);
+    }
+    const double* s = (const double*)src;
+    double* d = (double*)dst;
+    if (c->kernel == ACS_KERNEL_TEMPORAL) return launch_step_temporal<double>(c->dims, c->bc, k, s, d, c->g, c->cd, st);
+    if (c->kernel == ACS_KERNEL_TILED) return launch_step_tiled<double>(c->dims, c->bc, s, d, c->g, c->cd, st);
+    return launch_step_naive<double>(c->dims, c->bc, s, d, c->g, c->cd, st);
+}
+
+// Enqueue n steps; the state starts and ends in c->phi.  The launches are split
+// so that their number is even (ping-pong ends where it started); only n == 1
+// without temporal blocking, or an odd count of single steps, needs a final copy.
+static cudaError_t enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st) {
+    const int K = c->kernel == ACS_KERNEL_TEMPORAL ? c->depth : 1;
+    std::vector<int> sizes;
+    for (int64_t r = n; r > 0;) {
+        const int k = (int)std::min<int64_t>(K, r);
+        sizes.push_back(k);
+        r -= k;
+    }
+    if (sizes.size() % 2 == 1) {
+        for (size_t i = 0; i < sizes.size(); ++i)
+            if (sizes[i] >= 2) {
+                const int k = sizes[i];
+                sizes[i] = k / 2;
+                sizes.insert(sizes.begin() + i + 1, k - k / 2);
+                break;
+            }
+    }
+    const void* src = c->phi;
+    void* dst = c->other;
+    for (int k : sizes) {
+        cudaError_t e = launch_k(c, k, src, dst, st);
+        if (e != cudaSuccess) return e;
+        const void* t = src;
+        src = dst;
+        dst = const_cast<void*>(t);
+    }
+    if (src != c->phi) return cudaMemcpyAsync(c->phi, src, state_bytes(c), cudaMemcpyDeviceToDevice, st);
+    return cudaSuccess;
+}
+
+static int run_steps(acs_ctx* c, int64_t n) {
+    if (n <= 0) return ACS_OK;
+    if (c->grad.active) {
+        int rc = grad_record_steps(c, n);
+        if (rc) return rc;
+        c->steps_done += n;
+        return ACS_OK;
+    }
+    if (n < 4) {
+        if (enqueue_steps(c, n, c->stream) != cudaSuccess) return ACS_E_CUDA;
+        c->steps_done += n;
+        return ACS_OK;
+    }
+    GraphEntry* hit = nullptr;
+    for (auto& e : c->graphs)
+        if (e.nsteps == n && e.kernel == c->kernel && e.depth == c->depth && e.scheme == c->scheme) hit = &e;
+    if (!hit) {
+        if (c->graphs.size() >= 8) {
+            cudaGraphExecDestroy(c->graphs.front().exec);
+            c->graphs.erase(c->graphs.begin());
+        }
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ACS_E_CUDA;
+        cudaError_t e1 = enqueue_steps(c, n, c->cap);
+        cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return ACS_E_CUDA;
+        }
+        cudaGraphExec_t exec;
+        cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) return ACS_E_CUDA;
+        c->graphs.push_back(GraphEntry{n, c->kernel, c->depth, c->scheme, exec});
+        hit = &c->graphs.back();
+    }
+    if (cudaGraphLaunch(hit->exec, c->stream) != cudaSuccess) return ACS_E_CUDA;
+    c->steps_done += n;
+    return ACS_OK;
+}
+
+static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, cudaStream_t st) {
+    if (c->dtype == ACS_F32)
+        return launch_reduce<float>(c->dims, c->bc, (const float*)state, c->g, c->eps * c->eps, c->h,
+                                    c->partials, out2, st);
+    return launch_reduce<double>(c->dims, c->bc, (const double*)state, c->g, c->eps * c->eps, c->h,
+                                 c->partials, out2, st);
+}
+
+// ---------------------------------------------------------------- helpers for other units
+
+namespace acs {
+cudaError_t ctx_enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st) { return enqueue_steps(c, n, st); }
+cudaError_t ctx_launch_one(acs_ctx* c, const void* src, void* dst, cudaStream_t st) {
+    // one plain step with the naive kernel's arithmetic (identical bits to every variant)
+    if (c->dtype == ACS_F32)
+        return launch_step_naive<float>(c->dims, c->bc, (const float*)src, (float*)dst, c->g, c->cf, st);
+    return launch_step_naive<double>(c->dims, c->bc, (const double*)src, (double*)dst, c->g, c->cd, st);
+}
+CtxView ctx_view(acs_ctx* c) {
+    CtxView v;
+    v.dims = c->dims; v.bc = c->bc; v.dtype = c->dtype; v.g = c->g; v.esize = c->esize;
+    v.lam = c->lam; v.dt = c->dt; v.h = c->h; v.eps = c->eps;
+    v.phi = c->phi; v.other = c->other; v.stream = c->stream; v.partials = c->partials;
+    v.result = c->result; v.steps_done = c->steps_done; v.cf = c->cf; v.cd = c->cd; v.grad = &c->grad;
+    return v;
+}
+}  // namespace acs
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+ACS_API const char* acs_version(void) { return "0.1.0"; }
+
+ACS_API const char* acs_strerror(int s) {
+    switch (s) {
+        case ACS_OK: return "ok";
+        case ACS_WARN_MP_CONDITION: return "warning: dt > 1 - 2 d lambda, the maximum principle (Theorem 2) is not guaranteed";
+        case ACS_WARN_ENERGY_CONDITION: return "warning: dt > 4 (1 - 2 d lambda), energy decay (Theorem 3) is not guaranteed";
+        case ACS_E_INVAL: return "invalid argument";
+        case ACS_E_CUDA: return "CUDA runtime error";
+        case ACS_E_NOMEM: return "work buffer too small or host allocation failed";
+        case ACS_E_TIMEOUT: return "a bounded device-side wait gave up";
+        case ACS_E_NONFINITE: return "state is not finite (NaN or Inf)";
+        case ACS_E_STATE: return "call out of order (bind/set_state/record first)";
+        case ACS_E_UNSUPPORTED: return "kernel variant not available for this problem";
+        default: return "unknown status";
+    }
+}
+
+ACS_API int acs_dt_max(int dims, double eps, double h, double* dt_mp, double* dt_energy) {
+    if (dims < 1 || dims > 3 || !(eps >= 0) || !(h > 0) || !std::isfinite(eps) || !std::isfinite(h))
+        return ACS_E_INVAL;
+    const double r = eps * eps / (h * h);
+    // Theorem 2: dt <= 1 - 2 d lambda, lambda = r dt  =>  dt <= 1 / (1 + 2 d r)
+    if (dt_mp) *dt_mp = 1.0 / (1.0 + 2.0 * dims * r);
+    // Theorem 3: dt <= 4 (1 - 2 d lambda)  =>  dt <= 4 / (1 + 8 d r)
+    if (dt_energy) *dt_energy = 4.0 / (1.0 + 8.0 * dims * r);
+    return ACS_OK;
+}
+
+ACS_API int acs_create(int dims, const int64_t n[3], double eps, double dt, double h, int bc, int dtype,
+                       acs_ctx** out) {
+    if (!out || !n || dims < 1 || dims > 3) return ACS_E_INVAL;
+    if (!std::isfinite(eps) || !std::isfinite(dt) || !std::isfinite(h)) return ACS_E_INVAL;
+    if (eps < 0 || !(h > 0) || !(dt > 0) || !(dt < 2)) return ACS_E_INVAL;
+    if (bc < 0 || bc > 2 || (dtype != ACS_F32 && dtype != ACS_F64)) return ACS_E_INVAL;
+    int64_t total = 1;
+    for (int k = 0; k < dims; ++k) {
+        if (n[k] < 1 || n[k] > (int64_t(1) << 40)) return ACS_E_INVAL;
+        total *= n[k];
+        if (total > (int64_t(1) << 40)) return ACS_E_INVAL;
+    }
+    acs_ctx* c = new (std::nothrow) acs_ctx();
+    if (!c) return ACS_E_NOMEM;
+    c->dims = dims;
+    for (int k = 0; k < 3; ++k) c->n[k] = k < dims ? n[k] : 1;
+    c->eps = eps; c->dt = dt; c->h = h; c->bc = bc; c->dtype = dtype;
+    c->lam = eps * eps * dt / (h * h);
+    double dmp, den;
+    acs_dt_max(dims, eps, h, &dmp, &den);
+    c->mp_ok = dt <= dmp * (1.0 + 1e-12);
+    c->energy_ok = dt <= den * (1.0 + 1e-12);
+    c->g = make_geo(dims, c->n);
+    c->esize = dtype == ACS_F32 ? 4 : 8;
+    c->scheme = ACS_SCHEME_RLB_MIE_FD;
+    c->kernel_req = ACS_KERNEL_AUTO;
+    c->depth_req = 1;
+    c->kernel = ACS_KERNEL_NAIVE;
+    c->depth = 1;
+    refresh_coef(c);
+    c->bound = false;
+    c->phi = nullptr; c->work = nullptr; c->work_bytes = 0;
+    c->stream = nullptr; c->cap = nullptr;
+    c->steps_done = 0;
+    c->grad = GradState();
+    resolve_auto_kernel(c->dims, c->dtype, c->bc, c->g, &c->kernel, &c->depth);
+    *out = c;
+    if (!c->energy_ok) return ACS_WARN_ENERGY_CONDITION;
+    if (!c->mp_ok) return ACS_WARN_MP_CONDITION;
+    return ACS_OK;
+}
+
+ACS_API size_t acs_work_bytes(const acs_ctx* c) { return c ? work_total(c) : 0; }
+
+ACS_API int acs_bind(acs_ctx* c, void* d_phi, void* d_work, size_t work_bytes, void* stream) {
+    if (!c || !d_phi || !d_work) return ACS_E_INVAL;
+    if (((uintptr_t)d_phi % 16) || ((uintptr_t)d_work % kAlign)) return ACS_E_INVAL;
+    if (work_bytes < work_total(c)) return ACS_E_NOMEM;
+    if (!c->cap) {
+        if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return ACS_E_CUDA;
+    }
+    drop_graphs(c);
+    c->phi = d_phi;
+    c->work = (char*)d_work;
+    c->work_bytes = work_bytes;
+    c->stream = (cudaStream_t)stream;
+    c->other = c->work;
+    c->partials = (RedPartial*)(c->work + off_partials(c));
+    c->result = (double*)(c->work + off_result(c));
+    c->log = (double*)(c->work + off_log(c));
+    c->steps_done = 0;
+    c->bound = true;
+    return ACS_OK;
+}
+
+ACS_API int acs_set_scheme(acs_ctx* c, int scheme) {
+    if (!c || (scheme != ACS_SCHEME_RLB_MIE_FD && scheme != ACS_SCHEME_FEX_FD)) return ACS_E_INVAL;
+    c->scheme = scheme;
+    refresh_coef(c);
+    drop_graphs(c);
+    return ACS_OK;
+}
+
+ACS_API int acs_set_kernel(acs_ctx* c, int kernel, int depth) {
+    if (!c) return ACS_E_INVAL;
+    if (kernel == ACS_KERNEL_AUTO) {
+        c->kernel_req = kernel;
+        resolve_auto_kernel(c->dims, c->dtype, c->bc, c->g, &c->kernel, &c->depth);
+        drop_graphs(c);
+        return ACS_OK;
+    }
+    if (kernel == ACS_KERNEL_NAIVE) {
+        c->kernel_req = c->kernel = kernel;
+        c->depth = 1;
+        drop_graphs(c);
+        return ACS_OK;
+    }
+    if (kernel == ACS_KERNEL_TILED) {
+        if (!tiled_supported(c->dims, c->dtype, c->g)) return ACS_E_UNSUPPORTED;
+        c->kernel_req = c->kernel = kernel;
+        c->depth = 1;
+        drop_graphs(c);
+        return ACS_OK;
+    }
+    if (kernel == ACS_KERNEL_TEMPORAL) {
+        if (depth < 1 || depth > 8) return ACS_E_INVAL;
+        if (!temporal_supported(c->dims, c->dtype, depth, c->g)) return ACS_E_UNSUPPORTED;
+        c->kernel_req = c->kernel = kernel;
+        c->depth = depth;
+        drop_graphs(c);
+        return ACS_OK;
+    }
+    return ACS_E_INVAL;
+}
+
+ACS_API int acs_get_kernel(const acs_ctx* c, int* kernel, int* depth) {
+    if (!c) return ACS_E_INVAL;
+    if (kernel) *kernel = c->kernel;
+    if (depth) *depth = c->depth;
+    return ACS_OK;
+}
+
+ACS_API int acs_set_state(acs_ctx* c, const void* d_phi0) {
+    if (!c || !d_phi0) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    if (d_phi0 != c->phi &&
+        cudaMemcpyAsync(c->phi, d_phi0, state_bytes(c), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return ACS_E_CUDA;
+    c->steps_done = 0;
+    return grad_on_set_state(c);
+}
+
+ACS_API int acs_set_state_host(acs_ctx* c, const void* h_phi0) {
+    if (!c || !h_phi0) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    if (cudaMemcpyAsync(c->phi, h_phi0, state_bytes(c), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return ACS_E_CUDA;
+    c->steps_done = 0;
+    return grad_on_set_state(c);
+}
+
+ACS_API int acs_get_state_host(acs_ctx* c, void* h_phi) {
+    if (!c || !h_phi) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    if (cudaMemcpyAsync(h_phi, c->phi, state_bytes(c), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return ACS_E_CUDA;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+}
+
+ACS_API int acs_step(acs_ctx* c, int64_t n_steps) {
+    if (!c || n_steps < 0) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    return run_steps(c, n_steps);
+}
+
+ACS_API int64_t acs_steps_done(const acs_ctx* c) { return c ? c->steps_done : -1; }
+
+ACS_API int acs_observe_async(acs_ctx* c, double* d_out2) {
+    if (!c || !d_out2) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    return enqueue_reduce(c, c->phi, d_out2, c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+}
+
+static int observe_host(acs_ctx* c, double* e, double* m) {
+    if (!c->bound) return ACS_E_STATE;
+    if (enqueue_reduce(c, c->phi, c->result, c->stream) != cudaSuccess) return ACS_E_CUDA;
+    double hbuf[2];
+    if (cudaMemcpyAsync(hbuf, c->result, sizeof(hbuf), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return ACS_E_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;
+    if (e) *e = hbuf[0];
+    if (m) *m = hbuf[1];
+    const double v = e ? hbuf[0] : hbuf[1];
+    return std::isfinite(v) && std::isfinite(hbuf[1]) ? ACS_OK : ACS_E_NONFINITE;
+}
+
+ACS_API int acs_energy(acs_ctx* c, double* out_host) {
+    if (!c || !out_host) return ACS_E_INVAL;
+    return observe_host(c, out_host, nullptr);
+}
+
+ACS_API int acs_maxnorm(acs_ctx* c, double* out_host) {
+    if (!c || !out_host) return ACS_E_INVAL;
+    double m = 0.0;
+    int rc = observe_host(c, nullptr, &m);
+    *out_host = m;
+    return rc;
+}
+
+ACS_API int acs_run_logged(acs_ctx* c, int64_t n_steps, int64_t every, double* h_energy, double* h_maxnorm) {
+    if (!c || n_steps < 0 || every < 1 || !h_energy || !h_maxnorm) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    const int64_t entries = n_steps / every + 1;
+    if (entries > kLogCap) return ACS_E_INVAL;
+    if (enqueue_reduce(c, c->phi, c->log, c->stream) != cudaSuccess) return ACS_E_CUDA;
+    int64_t done = 0;
+    for (int64_t k = 1; k < entries; ++k) {
+        int rc = run_steps(c, every);
+        if (rc) return rc;
+        done += every;
+        if (enqueue_reduce(c, c->phi, c->log + 2 * k, c->stream) != cudaSuccess) return ACS_E_CUDA;
+    }
+    if (n_steps > done) {
+        int rc = run_steps(c, n_steps - done);
+        if (rc) return rc;
+    }
+    std::vector<double> buf(2 * entries);
+    if (cudaMemcpyAsync(buf.data(), c->log, sizeof(double) * 2 * entries, cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+        return ACS_E_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;
+    bool finite = true;
+    for (int64_t k = 0; k < entries; ++k) {
+        h_energy[k] = buf[2 * k];
+        h_maxnorm[k] = buf[2 * k + 1];
+        finite = finite && std::isfinite(buf[2 * k]) && std::isfinite(buf[2 * k + 1]);
+    }
+    return finite ? ACS_OK : ACS_E_NONFINITE;
+}
+
+ACS_API int acs_sync(acs_ctx* c) {
+    if (!c) return ACS_E_INVAL;
+    if (!c->bound) return ACS_OK;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+}
+
+ACS_API void acs_destroy(acs_ctx* c) {
+    if (!c) return;
+    if (c->bound) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// acs_device.cuh -- per-point arithmetic of the RLB-MIE-FD step, shared by every
+// stepping kernel so that all variants (naive, tiled, temporally blocked, batched)
+// produce bit-identical states.  The library is built with -fmad=false: every
+// fused multiply-add below is an explicit fma(), nothing is contracted behind
+// our back, and the order of every sum is fixed here.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "acs.h"
+
+namespace acs {
+
+// Coefficients of one step in the state's precision T.
+//   lam = eps^2 dt / h^2 (Eq. IE-FD-vector-form), a = dt/2, b = 1 - a.
+//   xi = c0 phi - a phi^3 + lam S, S = sum of the 2d neighbours, c0 = 1 - 2 d lam + a
+// (Remark 1's xi = (1 - 2 d lam) phi - (dt/2)(phi^3 - phi) + lam S, regrouped).
+// For the FEX-FD scheme of Remark 2 the same expression with a = dt,
+// c0 = 1 - 2 d lam + dt is the new state and no cubic is solved.
+template <typename T>
+struct Coef {
+    T lam, c0, a, b, rb, t, three_a;
+    T ymax;      // fast path of the cubic solve applies while y = t x^2 <= ymax
+    int newton;  // Newton corrections (1..3) after the series seed on the fast path
+    T clamp_hi;  // 1 + 16 ulp: overshoots up to this are rounding and go back to +-1
+    int clamp;   // 1: apply that rounding guard (set only when Theorem 2's condition holds)
+    int fex;     // 1: FEX-FD scheme (no cubic)
+};
+
+template <typename T> __device__ __forceinline__ T dfma(T a, T b, T c);
+template <> __device__ __forceinline__ float dfma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double dfma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Approximate reciprocal (relative error about 2^-22): good enough for a Newton
+// correction, whose own size is tiny.  FP64 goes through the FP32 unit on purpose.
+__device__ __forceinline__ float arcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double arcp(double x) { return (double)arcp((float)x); }
+
+// Robust root of a theta^3 + b theta = xi for any xi (used when the fast path does
+// not apply, e.g. when the maximum-principle condition is violated).  p is odd and
+// increasing, so solve for |xi| and restore the sign.  Newton from
+// min(|xi|/b, cbrt(|xi|/a)), two upper bounds of the root: p is convex on
+// theta > 0, so the iterates decrease monotonically to the root; stop when they
+// stop decreasing.  NaN propagates.
+template <typename T>
+__device__ __noinline__ T cubic_robust(T xi, T a, T b) {
+    T ax = xi < T(0) ? -xi : xi;
+    if (!(ax > T(0))) return xi;  // 0 or NaN
+    T th = ax / b;
+    T cb = cbrt(ax / a);
+    if (cb < th) th = cb;
+    for (int it = 0; it < 200; ++it) {
+        T th2 = th * th;
+        T p = dfma(dfma(a, th2, b), th, -ax);
+        T nt = th - p / dfma(T(3) * a, th2, b);
+        if (!(nt < th)) break;
+        th = nt;
+    }
+    return xi < T(0) ? -th : th;
+}
+
+// Root of theta + (dt/2) f(theta) = xi (Remark 1), i.e. a theta^3 + b theta = xi.
+// Fast path: with x = xi/b and y = (a/b) x^2 the root is x (1 - y + 3 y^2 - 12 y^3 + ...)
+// (Lagrange inversion, convergent for y < 4/27); its first three terms seed
+// `newton` Newton corrections.  The host picks `newton` and `ymax` from an
+// a-priori error bound so that the fast path is accurate to the last bit of T.
+template <typename T>
+__device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
+    const T x = xi * c.rb;
+    const T y = (c.t * x) * x;
+    T th;
+    if (y <= c.ymax) {
+        const T u = -y;
+        th = x * dfma(u, dfma(T(3), u, T(1)), T(1));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k < c.newton) {
+                const T th2 = th * th;
+                const T p = dfma(dfma(c.a, th2, c.b), th, -xi);
+                const T dp = dfma(c.three_a, th2, c.b);
+                th = dfma(-p, arcp(dp), th);
+            }
+        }
+    } else {
+        th = cubic_robust(xi, c.a, c.b);
+    }
+    if (c.clamp) {
+        if (th > T(1) && th <= c.clamp_hi) th = T(1);
+        else if (th < T(-1) && th >= -c.clamp_hi) th = T(-1);
+    }
+    return th;
+}
+
+// The new value of one unknown from its old value p and the sum s of its 2d
+// ghost-ruled neighbours.
+template <typename T>
+__device__ __forceinline__ T update(T p, T s, const Coef<T>& c) {
+    const T p2 = p * p;
+    const T xi = dfma(c.lam, s, p * dfma(-c.a, p2, c.c0));
+    if (c.fex) return xi;
+    return cubic_root(xi, c);
+}
+
+// Fixed summation order of the neighbours: z pair, then y pair, then x pair.
+template <typename T>
+__device__ __forceinline__ T nsum(T xm, T xp) { return xm + xp; }
+template <typename T>
+__device__ __forceinline__ T nsum(T ym, T yp, T xm, T xp) { return (ym + yp) + (xm + xp); }
+template <typename T>
+__device__ __forceinline__ T nsum(T zm, T zp, T ym, T yp, T xm, T xp) {
+    return ((zm + zp) + (ym + yp)) + (xm + xp);
+}
+
+// Geometry: the fastest axis is x (n[dims-1]); then y, then z.  Absent axes have size 1.
+struct Geo {
+    int64_t nx, ny, nz;  // sizes
+    int64_t sy, sz;      // strides of y and z (x stride is 1)
+    int64_t total;
+};
+
+}  // namespace acs

@@ -1,0 +1,56 @@
+// acs_host.h -- host-side pieces shared by the translation units of libacs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "acs_kernels.cuh"
+
+namespace acs {
+
+// Adjoint recording state of a context (see acs_grad_bind in acs.h).
+struct GradState {
+    bool active = false;
+    char* buf = nullptr;
+    size_t bytes = 0;
+    int64_t max_steps = 0, every = 1;
+    int64_t recorded = 0;  // steps recorded since the last set_state
+    bool started = false;  // checkpoint 0 holds phi^0
+};
+
+// What the other translation units may see of a context.
+struct CtxView {
+    int dims, bc, dtype;
+    Geo g;
+    size_t esize;
+    double lam, dt, h, eps;
+    void* phi;
+    void* other;
+    cudaStream_t stream;
+    RedPartial* partials;
+    double* result;
+    int64_t steps_done;
+    Coef<float> cf;
+    Coef<double> cd;
+    GradState* grad;
+};
+
+template <typename T>
+Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok);
+Geo make_geo(int dims, const int64_t* n);
+
+// Kernel choice for ACS_KERNEL_AUTO (autotune cache, else a static rule).
+void resolve_auto_kernel(int dims, int dtype, int bc, const Geo& g, int* kernel, int* depth);
+
+// Implemented in acs_api.cu for the adjoint unit.
+cudaError_t ctx_enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st);
+cudaError_t ctx_launch_one(acs_ctx* c, const void* src, void* dst, cudaStream_t st);
+CtxView ctx_view(acs_ctx* c);
+
+// Implemented in adjoint.cu.
+int grad_on_set_state(acs_ctx* c);
+int grad_record_steps(acs_ctx* c, int64_t n);
+
+}  // namespace acs

@@ -1,0 +1,37 @@
+// acs_kernels.cuh -- launchers of the device kernels, called by the host API.
+#pragma once
+
+#include <algorithm>
+
+#include "acs_device.cuh"
+
+namespace acs {
+
+// Reduction partial of one block: compensated FP64 sums of the bulk term
+// sum (phi^2 - 1)^2 / 4 and of the squared link differences, and max |phi|.
+struct RedPartial {
+    double bulk_s, bulk_c, link_s, link_c, mx, pad0, pad1, pad2;
+};
+constexpr int kMaxRedBlocks = 1024;
+
+template <typename T>
+cudaError_t launch_step_naive(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c,
+                              cudaStream_t st);
+
+// Tiled variants: return cudaErrorNotSupported when the shape is not covered.
+template <typename T>
+cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* dst, const Geo& g,
+                                 const Coef<T>& c, cudaStream_t st);
+bool tiled_supported(int dims, int dtype, const Geo& g);
+bool temporal_supported(int dims, int dtype, int depth, const Geo& g);
+
+// E_h and max |phi|: partials then a one-block finish writing {E_h, max} to out2.
+int reduce_blocks(const Geo& g);
+template <typename T>
+cudaError_t launch_reduce(int dims, int bc, const T* src, const Geo& g, double eps2, double h,
+                          RedPartial* partials, double* out2, cudaStream_t st);
+
+}  // namespace acs

@@ -1,0 +1,278 @@
+// adjoint.cu -- the hand-written adjoint of the discrete RLB-MIE-FD stepper.
+//
+// One step (Eq. IE-FD, Remark 1) maps phi^n to phi^{n+1} pointwise through
+//   xi_i = c0 phi_i - a phi_i^3 + lambda sum_nbr phi,   a theta^3 + b theta = xi_i,
+// (a = dt/2, b = 1 - a, c0 = 1 - 2 d lambda + a).  Implicit differentiation of the
+// cubic gives d theta / d xi = 1 / (3 a theta^2 + b), so for a terminal loss with
+// adjoint state adj^{n+1} = dL/dphi^{n+1}:
+//   mu_i    = adj^{n+1}_i / (3 a (phi^{n+1}_i)^2 + b)
+//   adj^n_j = mu_j (c0 - 3 a (phi^n_j)^2) + lambda sum_nbr(j) mu
+// (the ghost-rule stencil is symmetric -- the matrices D of Eq. Ddeltax are -- so
+// its transpose is the same stencil applied to mu), and since lambda = eps^2 dt/h^2
+// with dt, h fixed,
+//   dL/d(eps^2) += (dt/h^2) sum_i mu_i (sum_nbr(i) phi^n - 2 d phi^n_i).
+// The eps^2 sums are accumulated in FP64 with compensation, per step in a fixed
+// order (deterministic).  Forward states are checkpointed every `every` steps and
+// each segment is recomputed (with the forward kernel's arithmetic, so bit for bit
+// the same states) before its backward sweep.
+#include <cmath>
+#include <cstring>
+
+#include "acs_host.h"
+#include "acs_reduce.cuh"
+
+namespace acs {
+
+template <int BC, typename T>
+__device__ __forceinline__ T gnb(const T* __restrict__ p, int64_t i, int64_t c, int64_t n, int64_t s, int dir) {
+    if (dir < 0) {
+        if (c > 0) return p[i - s];
+        if (BC == ACS_BC_PERIODIC) return p[i + (n - 1) * s];
+        if (BC == ACS_BC_NEUMANN) return p[i];
+        return T(0);
+    }
+    if (c < n - 1) return p[i + s];
+    if (BC == ACS_BC_PERIODIC) return p[i - (n - 1) * s];
+    if (BC == ACS_BC_NEUMANN) return p[i];
+    return T(0);
+}
+
+// mu at the (ghost-ruled) neighbour: the ghost of mu follows the same rule as phi.
+template <int BC, typename T>
+__device__ __forceinline__ T mu_nb(const T* __restrict__ adj1, const T* __restrict__ th1, int64_t i, int64_t c,
+                                   int64_t n, int64_t s, int dir, const Coef<T>& cf) {
+    int64_t j;
+    if (dir < 0) {
+        if (c > 0) j = i - s;
+        else if (BC == ACS_BC_PERIODIC) j = i + (n - 1) * s;
+        else if (BC == ACS_BC_NEUMANN) j = i;
+        else return T(0);
+    } else {
+        if (c < n - 1) j = i + s;
+        else if (BC == ACS_BC_PERIODIC) j = i - (n - 1) * s;
+        else if (BC == ACS_BC_NEUMANN) j = i;
+        else return T(0);
+    }
+    const T t = th1[j];
+    return adj1[j] / dfma(cf.three_a, t * t, cf.b);
+}
+
+template <typename T, int D, int BC>
+__global__ void __launch_bounds__(256) k_adjoint(const T* __restrict__ phin, const T* __restrict__ phin1,
+                                                 const T* __restrict__ adj1, T* __restrict__ adj0, Geo g,
+                                                 Coef<T> cf, CSum* part) {
+    CSum ge{0.0, 0.0};
+    const int64_t rows = g.ny * g.nz;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t z = r / g.ny, y = r - z * g.ny;
+        const int64_t row = z * g.sz + y * g.sy;
+        for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) {
+            const int64_t i = row + x;
+            const T t = phin1[i];
+            const T mu = adj1[i] / dfma(cf.three_a, t * t, cf.b);
+            const T p = phin[i];
+            T smu, sphi;
+            {
+                const T mxm = mu_nb<BC>(adj1, phin1, i, x, g.nx, 1, -1, cf);
+                const T mxp = mu_nb<BC>(adj1, phin1, i, x, g.nx, 1, +1, cf);
+                const T pxm = gnb<BC>(phin, i, x, g.nx, 1, -1), pxp = gnb<BC>(phin, i, x, g.nx, 1, +1);
+                if (D == 1) {
+                    smu = nsum(mxm, mxp);
+                    sphi = nsum(pxm, pxp);
+                } else {
+                    const T mym = mu_nb<BC>(adj1, phin1, i, y, g.ny, g.sy, -1, cf);
+                    const T myp = mu_nb<BC>(adj1, phin1, i, y, g.ny, g.sy, +1, cf);
+                    const T pym = gnb<BC>(phin, i, y, g.ny, g.sy, -1), pyp = gnb<BC>(phin, i, y, g.ny, g.sy, +1);
+                    if (D == 2) {
+                        smu = nsum(mym, myp, mxm, mxp);
+                        sphi = nsum(pym, pyp, pxm, pxp);
+                    } else {
+                        const T mzm = mu_nb<BC>(adj1, phin1, i, z, g.nz, g.sz, -1, cf);
+                        const T mzp = mu_nb<BC>(adj1, phin1, i, z, g.nz, g.sz, +1, cf);
+                        const T pzm = gnb<BC>(phin, i, z, g.nz, g.sz, -1), pzp = gnb<BC>(phin, i, z, g.nz, g.sz, +1);
+                        smu = nsum(mzm, mzp, mym, myp, mxm, mxp);
+                        sphi = nsum(pzm, pzp, pym, pyp, pxm, pxp);
+                    }
+                }
+            }
+            adj0[i] = dfma(cf.lam, smu, mu * dfma(-cf.three_a, p * p, cf.c0));
+            cadd(ge, (double)mu * ((double)sphi - 2.0 * D * (double)p));
+        }
+    }
+    __shared__ CSum scratch[32];
+    ge = block_csum(ge, scratch);
+    if (threadIdx.x == 0) part[blockIdx.x] = ge;
+}
+
+// acc += sum of the step's partials, in a fixed order.
+__global__ void k_adjoint_finish(const CSum* part, int nparts, CSum* acc) {
+    CSum s{0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s = cmerge(s, part[i]);
+    __shared__ CSum scratch[32];
+    s = block_csum(s, scratch);
+    if (threadIdx.x == 0) acc[0] = cmerge(acc[0], s);
+}
+
+__global__ void k_zero_acc(CSum* acc) { acc[0] = CSum{0.0, 0.0}; }
+
+template <typename T>
+static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin1, const T* adj1, T* adj0,
+                                  const Geo& g, const Coef<T>& cf, CSum* part, CSum* acc, cudaStream_t st) {
+    const int nb = reduce_blocks(g);
+#define ACS_ADJ_CASE(D, B) \
+    if (dims == D && bc == B) k_adjoint<T, D, B><<<nb, 256, 0, st>>>(phin, phin1, adj1, adj0, g, cf, part); else
+    ACS_ADJ_CASE(1, 0) ACS_ADJ_CASE(1, 1) ACS_ADJ_CASE(1, 2)
+    ACS_ADJ_CASE(2, 0) ACS_ADJ_CASE(2, 1) ACS_ADJ_CASE(2, 2)
+    ACS_ADJ_CASE(3, 0) ACS_ADJ_CASE(3, 1) ACS_ADJ_CASE(3, 2)
+    return cudaErrorInvalidValue;
+#undef ACS_ADJ_CASE
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adjoint_finish<<<1, 256, 0, st>>>(part, nb, acc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- recording layout
+
+namespace {
+constexpr size_t kA = 256;
+size_t al(size_t x) { return (x + kA - 1) / kA * kA; }
+
+struct GradLayout {
+    size_t sb;        // aligned state bytes
+    int64_t nckpt;    // checkpoint slots
+    size_t ckpt, seg, adjA, adjB, part, acc, total;
+};
+
+GradLayout layout(const CtxView& v, int64_t max_steps, int64_t every) {
+    GradLayout L;
+    L.sb = al((size_t)v.g.total * v.esize);
+    L.nckpt = max_steps / every + 1;
+    L.ckpt = 0;
+    L.seg = L.ckpt + L.sb * (size_t)L.nckpt;
+    L.adjA = L.seg + L.sb * (size_t)every;
+    L.adjB = L.adjA + L.sb;
+    L.part = L.adjB + L.sb;
+    L.acc = L.part + al(sizeof(CSum) * kMaxRedBlocks);
+    L.total = L.acc + kA;
+    return L;
+}
+}  // namespace
+
+int grad_on_set_state(acs_ctx* c) {
+    CtxView v = ctx_view(c);
+    GradState& G = *v.grad;
+    if (!G.active) return ACS_OK;
+    GradLayout L = layout(v, G.max_steps, G.every);
+    if (cudaMemcpyAsync(G.buf + L.ckpt, v.phi, (size_t)v.g.total * v.esize, cudaMemcpyDeviceToDevice, v.stream) !=
+        cudaSuccess)
+        return ACS_E_CUDA;
+    G.recorded = 0;
+    G.started = true;
+    return ACS_OK;
+}
+
+int grad_record_steps(acs_ctx* c, int64_t n) {
+    CtxView v = ctx_view(c);
+    GradState& G = *v.grad;
+    if (!G.started) return ACS_E_STATE;
+    if (G.recorded + n > G.max_steps) return ACS_E_NOMEM;
+    GradLayout L = layout(v, G.max_steps, G.every);
+    while (n > 0) {
+        const int64_t room = G.every - (G.recorded % G.every);
+        const int64_t k = std::min(n, room);
+        if (ctx_enqueue_steps(c, k, v.stream) != cudaSuccess) return ACS_E_CUDA;
+        G.recorded += k;
+        n -= k;
+        if (G.recorded % G.every == 0) {
+            char* slot = G.buf + L.ckpt + L.sb * (size_t)(G.recorded / G.every);
+            if (cudaMemcpyAsync(slot, v.phi, (size_t)v.g.total * v.esize, cudaMemcpyDeviceToDevice, v.stream) !=
+                cudaSuccess)
+                return ACS_E_CUDA;
+        }
+    }
+    return ACS_OK;
+}
+
+}  // namespace acs
+
+using namespace acs;
+
+extern "C" {
+
+ACS_API size_t acs_grad_work_bytes(const acs_ctx* c, int64_t max_steps, int64_t every) {
+    if (!c || max_steps < 1 || every < 1) return 0;
+    CtxView v = ctx_view(const_cast<acs_ctx*>(c));
+    return layout(v, max_steps, every).total;
+}
+
+ACS_API int acs_grad_bind(acs_ctx* c, void* d_grad_work, size_t bytes, int64_t max_steps, int64_t every) {
+    if (!c || !d_grad_work || max_steps < 1 || every < 1 || ((uintptr_t)d_grad_work % 256)) return ACS_E_INVAL;
+    CtxView v = ctx_view(c);
+    if (!v.phi) return ACS_E_STATE;
+    GradLayout L = layout(v, max_steps, every);
+    if (bytes < L.total) return ACS_E_NOMEM;
+    GradState& G = *v.grad;
+    G.active = true;
+    G.buf = (char*)d_grad_work;
+    G.bytes = bytes;
+    G.max_steps = max_steps;
+    G.every = every;
+    G.recorded = 0;
+    G.started = false;
+    // record from the current state
+    return grad_on_set_state(c);
+}
+
+ACS_API int acs_grad(acs_ctx* c, const void* d_dL_dphiT, void* d_dL_dphi0, double* dL_deps2_host) {
+    if (!c || !d_dL_dphiT || !d_dL_dphi0 || !dL_deps2_host) return ACS_E_INVAL;
+    CtxView v = ctx_view(c);
+    GradState& G = *v.grad;
+    if (!G.active || !G.started) return ACS_E_STATE;
+    if (v.cf.fex) return ACS_E_UNSUPPORTED;
+    const GradLayout L = layout(v, G.max_steps, G.every);
+    const size_t bytes = (size_t)v.g.total * v.esize;
+    cudaStream_t st = v.stream;
+    char* A = G.buf + L.adjA;
+    char* B = G.buf + L.adjB;
+    CSum* part = (CSum*)(G.buf + L.part);
+    CSum* acc = (CSum*)(G.buf + L.acc);
+    if (cudaMemcpyAsync(A, d_dL_dphiT, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return ACS_E_CUDA;
+    k_zero_acc<<<1, 1, 0, st>>>(acc);
+    const int64_t N = G.recorded;
+    if (N > 0) {
+        for (int64_t seg = (N - 1) / G.every; seg >= 0; --seg) {
+            const int64_t s0 = seg * G.every;
+            const int64_t m = std::min(G.every, N - s0);
+            char* ck = G.buf + L.ckpt + L.sb * (size_t)seg;
+            // recompute phi^{s0+1} .. phi^{s0+m} into the segment buffer
+            const char* prev = ck;
+            for (int64_t j = 0; j < m; ++j) {
+                char* dst = G.buf + L.seg + L.sb * (size_t)j;
+                if (ctx_launch_one(c, prev, dst, st) != cudaSuccess) return ACS_E_CUDA;
+                prev = dst;
+            }
+            for (int64_t k = m - 1; k >= 0; --k) {
+                const char* pk = k == 0 ? ck : G.buf + L.seg + L.sb * (size_t)(k - 1);
+                const char* pk1 = G.buf + L.seg + L.sb * (size_t)k;
+                cudaError_t e;
+                if (v.dtype == ACS_F32)
+                    e = launch_adjoint<float>(v.dims, v.bc, (const float*)pk, (const float*)pk1, (const float*)A,
+                                              (float*)B, v.g, v.cf, part, acc, st);
+                else
+                    e = launch_adjoint<double>(v.dims, v.bc, (const double*)pk, (const double*)pk1,
+                                               (const double*)A, (double*)B, v.g, v.cd, part, acc, st);
+                if (e != cudaSuccess) return ACS_E_CUDA;
+                std::swap(A, B);
+            }
+        }
+    }
+    if (cudaMemcpyAsync(d_dL_dphi0, A, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return ACS_E_CUDA;
+    CSum h;
+    if (cudaMemcpyAsync(&h, acc, sizeof(CSum), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ACS_E_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ACS_E_CUDA;
+    *dL_deps2_host = (h.s + h.c) * (v.dt / (v.h * v.h));
+    return std::isfinite(*dL_deps2_host) ? ACS_OK : ACS_E_NONFINITE;
+}
+
+}  // extern "C"

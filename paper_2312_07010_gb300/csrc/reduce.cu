@@ -1,0 +1,130 @@
+// reduce.cu -- the discrete free energy E_h (Theorem 3, Eq. proof2-eq0) and the
+// maximum norm (Theorem 2) of a state, in FP64 with compensated sums.
+//
+// E_h = h^d [ 1/4 sum_i (phi_i^2 - 1)^2 - eps^2/2 Phi^T Lambda_{dx} Phi ], and
+// -Phi^T Lambda_{dx} Phi = h^-2 sum over lattice links of the squared difference
+// (the matrices D of Eq. Ddeltax are symmetric, so the quadratic form is a sum of
+// squares): interior links along every axis; periodic adds the wrap-around link
+// of every line; Dirichlet adds the links from the first and last unknown of
+// every line to the zero boundary value; Neumann adds nothing.  The sum of squares
+// has no cancellation, unlike the phi . (Lambda phi) form.
+//
+// Two stages, deterministic: a fixed grid (depending only on the shape) writes one
+// partial per block; one block combines them in a fixed order.  Each thread sums
+// with Neumaier's compensation; partials are combined with error-free TwoSum.
+#include "acs_kernels.cuh"
+#include "acs_reduce.cuh"
+
+namespace acs {
+
+template <int BC>
+__device__ __forceinline__ void axis_links(CSum& acc, double p, double up, int64_t c, int64_t n) {
+    // the link from this unknown to the next one along the axis (if any), and the
+    // Dirichlet link from the first unknown down to the boundary value
+    if (c < n - 1) {
+        const double d = up - p;
+        cadd(acc, d * d);
+    } else if (BC == ACS_BC_PERIODIC) {
+        const double d = up - p;  // `up` is the wrap-around neighbour here
+        cadd(acc, d * d);
+    } else if (BC == ACS_BC_DIRICHLET) {
+        cadd(acc, p * p);
+    }
+    if (BC == ACS_BC_DIRICHLET && c == 0) cadd(acc, p * p);
+}
+
+template <typename T, int D, int BC>
+__global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g, RedPartial* part) {
+    CSum bulk{0.0, 0.0}, link{0.0, 0.0};
+    double mx = 0.0;
+    const int64_t rows = g.ny * g.nz;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t z = r / g.ny, y = r - z * g.ny;
+        const int64_t row = z * g.sz + y * g.sy;
+        for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) {
+            const int64_t i = row + x;
+            const double p = (double)src[i];
+            const double w = p * p - 1.0;
+            cadd(bulk, 0.25 * w * w);
+            mx = nmax(mx, fabs(p));
+            axis_links<BC>(link, p, (double)src[x < g.nx - 1 ? i + 1 : row], x, g.nx);
+            if (D >= 2)
+                axis_links<BC>(link, p, (double)src[y < g.ny - 1 ? i + g.sy : z * g.sz + x], y, g.ny);
+            if (D >= 3)
+                axis_links<BC>(link, p, (double)src[z < g.nz - 1 ? i + g.sz : y * g.sy + x], z, g.nz);
+        }
+    }
+    // warp then block combination in a fixed order
+    for (int off = 16; off > 0; off >>= 1) {
+        bulk = cmerge(bulk, shfl_down(bulk, off));
+        link = cmerge(link, shfl_down(link, off));
+        mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    }
+    __shared__ CSum sb[8], sl[8];
+    __shared__ double sm[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sb[warp] = bulk; sl[warp] = link; sm[warp] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CSum B = sb[0], L = sl[0];
+        double M = sm[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { B = cmerge(B, sb[w]); L = cmerge(L, sl[w]); M = nmax(M, sm[w]); }
+        part[blockIdx.x] = RedPartial{B.s, B.c, L.s, L.c, M, 0.0, 0.0, 0.0};
+    }
+}
+
+__global__ void k_reduce_finish(const RedPartial* part, int nparts, double hd, double link_scale,
+                                double* out2) {
+    CSum B{0.0, 0.0}, L{0.0, 0.0};
+    double M = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        B = cmerge(B, CSum{part[i].bulk_s, part[i].bulk_c});
+        L = cmerge(L, CSum{part[i].link_s, part[i].link_c});
+        M = nmax(M, part[i].mx);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        B = cmerge(B, shfl_down(B, off));
+        L = cmerge(L, shfl_down(L, off));
+        M = nmax(M, __shfl_down_sync(0xffffffffu, M, off));
+    }
+    __shared__ CSum sb[8], sl[8];
+    __shared__ double sm[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sb[warp] = B; sl[warp] = L; sm[warp] = M; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { sb[0] = cmerge(sb[0], sb[w]); sl[0] = cmerge(sl[0], sl[w]); sm[0] = nmax(sm[0], sm[w]); }
+        const double bulk = sb[0].s + sb[0].c;
+        const double links = sl[0].s + sl[0].c;
+        out2[0] = hd * (bulk + link_scale * links);
+        out2[1] = sm[0];
+    }
+}
+
+int reduce_blocks(const Geo& g) {
+    const int64_t rows = g.ny * g.nz;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(rows, kMaxRedBlocks));
+}
+
+template <typename T>
+cudaError_t launch_reduce(int dims, int bc, const T* src, const Geo& g, double eps2, double h,
+                          RedPartial* partials, double* out2, cudaStream_t st) {
+    const int nb = reduce_blocks(g);
+#define ACS_RED_CASE(D, B) \
+    if (dims == D && bc == B) k_reduce<T, D, B><<<nb, 256, 0, st>>>(src, g, partials); else
+    ACS_RED_CASE(1, 0) ACS_RED_CASE(1, 1) ACS_RED_CASE(1, 2)
+    ACS_RED_CASE(2, 0) ACS_RED_CASE(2, 1) ACS_RED_CASE(2, 2)
+    ACS_RED_CASE(3, 0) ACS_RED_CASE(3, 1) ACS_RED_CASE(3, 2)
+    return cudaErrorInvalidValue;
+#undef ACS_RED_CASE
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const double hd = std::pow(h, (double)dims);
+    k_reduce_finish<<<1, 256, 0, st>>>(partials, nb, hd, 0.5 * eps2 / (h * h), out2);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_reduce<float>(int, int, const float*, const Geo&, double, double, RedPartial*, double*, cudaStream_t);
+template cudaError_t launch_reduce<double>(int, int, const double*, const Geo&, double, double, RedPartial*, double*, cudaStream_t);
+
+}  // namespace acs

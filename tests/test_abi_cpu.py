@@ -1,0 +1,119 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol include/acs.h
+declares, and its host-only logic (argument validation, step-size conditions,
+status strings) behaves as documented.  No call here touches a device."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "acs.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2312_07010_gb300 import build, lib
+    build.build()
+    return lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"ACS_API\s+[\w\s\*]+?\b(acs_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("acs_create", "acs_step", "acs_energy", "acs_maxnorm", "acs_grad", "acs_bind",
+              "acs_batch_create", "acs_batch_step"):
+        assert s in syms
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2312_07010_gb300 import SIGNATURES
+    missing = [s for s in declared_symbols() if not hasattr(L, s)]
+    assert not missing, missing
+    assert sorted(SIGNATURES) == declared_symbols()
+
+
+def _create(L, dims, n, eps, dt, h, bc, dtype=0):
+    ctx = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    rc = L.acs_create(dims, arr, eps, dt, h, bc, dtype, ctypes.byref(ctx))
+    return rc, ctx
+
+
+def test_create_validates_arguments(L):
+    good = (2, (8, 8), 0.02, 0.01, 1 / 8, 0)
+    rc, ctx = _create(L, *good)
+    assert rc == 0 and ctx.value
+    L.acs_destroy(ctx)
+    bad = [
+        (0, (8,), 0.02, 0.01, 0.1, 0), (4, (8, 8, 8), 0.02, 0.01, 0.1, 0),
+        (1, (0,), 0.02, 0.01, 0.1, 0), (2, (8, -1), 0.02, 0.01, 0.1, 0),
+        (1, (8,), -0.1, 0.01, 0.1, 0), (1, (8,), 0.02, 0.0, 0.1, 0), (1, (8,), 0.02, 2.0, 0.1, 0),
+        (1, (8,), 0.02, 0.01, 0.0, 0), (1, (8,), 0.02, 0.01, 0.1, 3), (1, (8,), math.nan, 0.01, 0.1, 0),
+        (1, (8,), 0.02, math.inf, 0.1, 0), (3, (1 << 14, 1 << 14, 1 << 14), 0.02, 0.01, 0.1, 0),
+    ]
+    for args in bad:
+        rc, ctx = _create(L, *args)
+        assert rc == -1, args
+        assert not ctx.value
+    rc, ctx = _create(L, 1, (8,), 0.02, 0.01, 0.1, 0, dtype=7)
+    assert rc == -1
+
+
+def test_create_warns_on_step_conditions(L):
+    h = 1 / 64
+    eps = 8 * math.tanh(0.9) * h / math.sqrt(2)
+    # dt = 5 h^2 satisfies Theorem 2; dt = 1/5 (lambda = 3.28) violates Theorems 2 and 3
+    rc, ctx = _create(L, 1, (193,), eps, 5 * h * h, h, 1)
+    assert rc == 0
+    L.acs_destroy(ctx)
+    rc, ctx = _create(L, 1, (193,), eps, 0.2, h, 1)
+    assert rc == 2
+    L.acs_destroy(ctx)
+    # between the two bounds: only the maximum principle warning
+    dmp = ctypes.c_double()
+    den = ctypes.c_double()
+    assert L.acs_dt_max(1, 0.1, 0.1, ctypes.byref(dmp), ctypes.byref(den)) == 0
+    rc, ctx = _create(L, 1, (16,), 0.1, 0.5 * (dmp.value + den.value), 0.1, 0)
+    assert rc == 1
+    L.acs_destroy(ctx)
+
+
+def test_dt_max_matches_the_theorems(L):
+    for d in (1, 2, 3):
+        for eps, h in ((0.02, 1 / 128), (0.01, 1 / 512), (0.3, 0.1)):
+            a = ctypes.c_double()
+            b = ctypes.c_double()
+            assert L.acs_dt_max(d, eps, h, ctypes.byref(a), ctypes.byref(b)) == 0
+            lam = eps * eps * a.value / (h * h)
+            assert a.value == pytest.approx(1 - 2 * d * lam, rel=1e-14)        # Theorem 2 at equality
+            lam = eps * eps * b.value / (h * h)
+            assert b.value == pytest.approx(4 * (1 - 2 * d * lam), rel=1e-14)  # Theorem 3 at equality
+    assert L.acs_dt_max(0, 0.1, 0.1, None, None) == -1
+
+
+def test_strerror_and_version(L):
+    for s in (0, 1, 2, -1, -2, -3, -4, -5, -6, -7, 99):
+        assert isinstance(L.acs_strerror(s), bytes) and L.acs_strerror(s)
+    assert re.match(rb"^\d+\.\d+\.\d+$", L.acs_version())
+
+
+def test_unbound_context_rejects_device_calls(L):
+    rc, ctx = _create(L, 2, (8, 8), 0.02, 0.01, 1 / 8, 0)
+    assert rc == 0
+    assert L.acs_step(ctx, 1) == -6
+    v = ctypes.c_double()
+    assert L.acs_energy(ctx, ctypes.byref(v)) == -6
+    assert L.acs_step(ctx, -1) == -1
+    assert L.acs_work_bytes(ctx) >= 8 * 8 * 4
+    assert L.acs_set_kernel(ctx, 9, 1) == -1
+    assert L.acs_set_kernel(ctx, 3, 0) == -1
+    assert L.acs_set_scheme(ctx, 5) == -1
+    L.acs_destroy(ctx)
+    L.acs_destroy(None)

@@ -1,0 +1,212 @@
+"""GPU parity of the CUDA stepper against the FP64 oracle, through the C ABI.
+
+Tolerances (written per test):
+  FP64 state: max |gpu - oracle| / max |oracle| <= 1e-12 after the stated steps.
+  FP32 state: max |gpu - oracle| <= 2e-5 (oracle started from the FP32-rounded
+              phi0), and |phi| <= 1 exactly while Theorem 2's condition holds.
+  Reductions: E_h and max|phi| of the same state, GPU (link form, compensated) vs
+              oracle (Phi^T Lambda Phi form): relative 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import BC_DIRICHLET, BC_NEUMANN, BC_PERIODIC, cfg1, cfg2, cfg3, dt_rule, uniform_field
+
+pytestmark = pytest.mark.gpu
+
+BCS = [BC_PERIODIC, BC_NEUMANN, BC_DIRICHLET]
+BCN = {0: "P", 1: "HN", 2: "HD"}
+SHAPES = {1: [(1,), (2,), (7,), (1000,), (4099,)],
+          2: [(1, 1), (2, 2), (5, 7), (33, 65), (128, 128), (130, 257)],
+          3: [(1, 1, 1), (4, 4, 4), (7, 6, 5), (33, 17, 9), (64, 64, 64), (20, 37, 70)]}
+
+
+@pytest.fixture(scope="module")
+def acs():
+    import paper_2312_07010_gb300 as P
+    P.build.build()
+    P.lib()
+    return P
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _problem(shape, bc, seed, eps=0.02):
+    d = len(shape)
+    h = 1.0 / max(shape)
+    dt = dt_rule(d, eps, h)
+    phi0 = uniform_field(shape, -1.0, 1.0, seed)
+    return h, eps, dt, phi0
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", [s for d in (1, 2, 3) for s in SHAPES[d]], ids=str)
+def test_fp64_parity_50_steps(acs, shape, bc):
+    h, eps, dt, phi0 = _problem(shape, bc, 17 + len(shape) + bc)
+    s = acs.AllenCahn(shape, eps, dt, h, bc, "f64")
+    s.set_state(phi0)
+    s.step(1)
+    one = s.numpy()
+    assert relerr(one, oracle.step_fd(phi0, eps, dt, h, bc)) <= 1e-13
+    s.step(49)
+    ref = oracle.run_fd(phi0, eps, dt, h, bc, 50)
+    assert relerr(s.numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", [(4099,), (130, 257), (20, 37, 70), (64, 64, 64)], ids=str)
+def test_fp32_parity_200_steps(acs, shape, bc):
+    h, eps, dt, phi0 = _problem(shape, bc, 29 + len(shape) + bc)
+    p32 = phi0.astype(np.float32)
+    s = acs.AllenCahn(shape, eps, dt, h, bc, "f32")
+    s.set_state(p32)
+    s.step(200)
+    got = s.numpy().astype(np.float64)
+    ref = oracle.run_fd(p32.astype(np.float64), eps, dt, h, bc, 200)
+    assert float(np.abs(got - ref).max()) <= 2e-5
+    assert float(np.abs(got).max()) <= 1.0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", [(9,), (5, 7), (33, 65), (7, 6, 5), (40, 33, 20)], ids=str)
+def test_energy_and_maxnorm_parity(acs, shape, bc, dtype):
+    h, eps, dt, phi0 = _problem(shape, bc, 41 + len(shape) + bc)
+    s = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    s.set_state(phi0)
+    s.step(3)
+    state = s.numpy().astype(np.float64)
+    E = s.energy()
+    M = s.maxnorm()
+    assert E == pytest.approx(oracle.energy(state, eps, dt, h, bc), rel=1e-12, abs=1e-300)
+    assert M == oracle.maxnorm(state)
+
+
+def test_cfg1_full_run(acs):
+    """2D 128^2 periodic, FP64, 1000 steps, E_h and max-norm every 10 steps."""
+    w = cfg1()
+    phi0 = w.phi0()
+    s = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f64")
+    s.set_state(phi0)
+    E, M = s.run_logged(w.steps, w.log_every)
+    got = s.numpy()
+    ref = phi0.copy()
+    refE = [oracle.energy(ref, w.eps, w.dt, w.h, w.bc)]
+    for k in range(w.steps // w.log_every):
+        ref = oracle.run_fd(ref, w.eps, w.dt, w.h, w.bc, w.log_every)
+        refE.append(oracle.energy(ref, w.eps, w.dt, w.h, w.bc))
+    assert relerr(got, ref) <= 1e-12
+    np.testing.assert_allclose(E, refE, rtol=1e-12)
+    assert np.all(np.diff(E) <= 0)
+    assert np.all(M <= 1.0)
+
+
+def test_step_calls_compose(acs):
+    """acs_step(n) (graph replay) equals n calls of acs_step(1), bit for bit."""
+    shape = (48, 40)
+    h, eps, dt, phi0 = _problem(shape, BC_NEUMANN, 3)
+    a = acs.AllenCahn(shape, eps, dt, h, BC_NEUMANN, "f32")
+    b = acs.AllenCahn(shape, eps, dt, h, BC_NEUMANN, "f32")
+    a.set_state(phi0)
+    b.set_state(phi0)
+    a.step(37)
+    for _ in range(37):
+        b.step(1)
+    assert np.array_equal(a.numpy(), b.numpy())
+    a.step(0)
+    assert a.steps_done == 37
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+def test_fex_scheme_parity(acs, bc):
+    shape = (21, 34)
+    h, eps, dt, phi0 = _problem(shape, bc, 8)
+    dt = 0.2 * dt
+    s = acs.AllenCahn(shape, eps, dt, h, bc, "f64")
+    s.set_scheme(acs.ACS_SCHEME_FEX_FD)
+    s.set_state(phi0)
+    s.step(20)
+    ref = oracle.run_fd(phi0, eps, dt, h, bc, 20, scheme=oracle.SCHEME_FEX_FD)
+    assert relerr(s.numpy(), ref) <= 1e-12
+
+
+def test_large_dt_robust_cubic(acs):
+    """Fig. 3(b): dt = 1/5 (lambda = 3.28) violates Theorem 2; |phi| exceeds 1 and the
+    robust cubic path must still match the oracle."""
+    h = 1 / 64
+    eps = 8 * math.tanh(0.9) * h / math.sqrt(2)
+    N = round(3 / h)
+    x = -0.5 + h * np.arange(N + 1)
+    phi0 = 0.5 * (1 - np.tanh(x / (2 * math.sqrt(2) * eps)))
+    s = acs.AllenCahn((N + 1,), eps, 0.2, h, BC_NEUMANN, "f64")
+    assert s.create_status == 2
+    s.set_state(phi0)
+    ref = phi0
+    worst = 0.0
+    for _ in range(6):
+        s.step(1)
+        ref = oracle.step_fd(ref, eps, 0.2, h, BC_NEUMANN)
+        assert relerr(s.numpy(), ref) <= 1e-12
+        worst = max(worst, s.maxnorm(allow_nonfinite=True))
+    assert worst > 1.0
+
+
+def test_nonfinite_state_is_reported(acs):
+    shape = (16, 16)
+    h, eps, dt, phi0 = _problem(shape, BC_PERIODIC, 5)
+    phi0[3, 4] = np.nan
+    s = acs.AllenCahn(shape, eps, dt, h, BC_PERIODIC, "f32")
+    s.set_state(phi0)
+    s.step(2)
+    with pytest.raises(acs.AcsError) as e:
+        s.maxnorm()
+    assert e.value.status == -5
+    assert math.isnan(s.maxnorm(allow_nonfinite=True))
+
+
+def test_cfg2_full_size_fp32(acs):
+    """3D 512^3 Neumann, FP32: one step against the oracle on the whole grid, then the
+    200-step run keeps |phi| <= 1 and a non-increasing E_h (logged every 50 steps)."""
+    w = cfg2("f32")
+    phi0 = w.phi0().astype(np.float32)
+    s = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    s.set_state(phi0)
+    s.step(1)
+    got = s.numpy()
+    ref = oracle.step_fd(phi0.astype(np.float64), w.eps, w.dt, w.h, w.bc)
+    assert float(np.abs(got - ref).max()) <= 2e-6
+    del got, ref
+    s.set_state(phi0)
+    E, M = s.run_logged(w.steps, 50)
+    assert np.all(np.diff(E) <= 0)
+    assert np.all(M <= 1.0)
+
+
+def test_cfg3_full_size_fp64(acs):
+    """2D 4096^2 Dirichlet star, FP64: 20 steps against the oracle on the whole grid."""
+    w = cfg3("f64")
+    phi0 = w.phi0()
+    s = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f64")
+    s.set_state(phi0)
+    s.step(20)
+    ref = oracle.run_fd(phi0, w.eps, w.dt, w.h, w.bc, 20)
+    assert relerr(s.numpy(), ref) <= 1e-12
+    assert s.energy() == pytest.approx(oracle.energy(ref, w.eps, w.dt, w.h, w.bc), rel=1e-12)
+
+
+def test_host_state_roundtrip(acs):
+    shape = (9, 10, 11)
+    h, eps, dt, phi0 = _problem(shape, BC_DIRICHLET, 12)
+    s = acs.AllenCahn(shape, eps, dt, h, BC_DIRICHLET, "f64")
+    host = torch.from_numpy(phi0.copy()).pin_memory()
+    s.set_state_host(host)
+    s.step(4)
+    out = torch.empty(shape, dtype=torch.float64).pin_memory()
+    s.get_state_host(out)
+    assert relerr(out.numpy(), oracle.run_fd(phi0, eps, dt, h, BC_DIRICHLET, 4)) <= 1e-13
