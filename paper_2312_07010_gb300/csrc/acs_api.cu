@@ -44,29 +44,60 @@ static void pick_newton(double t, double rb, double tol, int* newton, double* ym
     *ymax = lo;
 }
 
+// Lagrange-inversion coefficients C_k = binom(3k, k) / (2k + 1).
+static const double kLagrangeC[11] = {1, 1, 3, 12, 55, 273, 1428, 7752, 43263, 246675, 1430715};
+
+// Bound on the relative error of the series truncated after nt terms: the terms
+// alternate and shrink (ratio < 27y/4 < 1), so the first omitted term bounds it.
+static double series_bound(double y, int nt) {
+    if (y >= 4.0 / 27.0) return 1.0;
+    return kLagrangeC[nt] * std::pow(y, nt) / (1.0 - 6.75 * y);
+}
+
 template <typename T>
 Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
     Coef<T> c;
     std::memset(&c, 0, sizeof(c));
     const double a = 0.5 * dt, b = 1.0 - a;
+    const double tol = sizeof(T) == 4 ? std::ldexp(1.0, -26) : std::ldexp(1.0, -55);
     c.lam = (T)lam;
-    if (scheme == ACS_SCHEME_FEX_FD) {
-        c.a = (T)dt;
-        c.c0 = (T)(1.0 - 2.0 * dims * lam + dt);
-        c.fex = 1;
-    } else {
-        c.a = (T)a;
-        c.c0 = (T)(1.0 - 2.0 * dims * lam + a);
-        c.fex = 0;
-    }
     c.b = (T)b;
     c.rb = (T)(1.0 / b);
     c.t = (T)(a / b);
     c.three_a = (T)(3.0 * a);
-    const double tol = sizeof(T) == 4 ? std::ldexp(1.0, -26) : std::ldexp(1.0, -55);
-    double ymax;
-    pick_newton(a / b, 1.0 / b, tol, &c.newton, &ymax);
-    c.ymax = (T)ymax;
+    if (scheme == ACS_SCHEME_FEX_FD) {
+        c.a = (T)dt;
+        c.c0 = (T)(1.0 - 2.0 * dims * lam + dt);
+        c.solve = kSolveFex;
+    } else {
+        c.a = (T)a;
+        c.c0 = (T)(1.0 - 2.0 * dims * lam + a);
+        const int nt = SeriesTerms<T>::value;
+        const double t = a / b, rb = 1.0 / b;
+        const double yneed = t * (1.001 * rb) * (1.001 * rb);
+        if (series_bound(yneed, nt) <= tol) {
+            c.solve = kSolveSeries;
+            double lo = yneed, hi = 0.1;
+            if (series_bound(hi, nt) <= tol) lo = hi;
+            else
+                for (int it = 0; it < 80; ++it) {
+                    const double mid = 0.5 * (lo + hi);
+                    if (series_bound(mid, nt) <= tol) lo = mid; else hi = mid;
+                }
+            const double x2max = lo / (t * rb * rb);
+            c.xi2max = (T)std::min(x2max, 1e30);
+            double ak = 1.0;  // (-a)^k
+            for (int k = 0; k < nt; ++k) {
+                c.q[k] = (T)(kLagrangeC[k] * ak / std::pow(b, 3.0 * k + 1.0));
+                ak *= -a;
+            }
+        } else {
+            c.solve = kSolveNewton;
+        }
+        double ymax;
+        pick_newton(t, rb, tol, &c.newton, &ymax);
+        c.ymax = (T)ymax;
+    }
     const double ulp1 = sizeof(T) == 4 ? std::ldexp(1.0, -23) : std::ldexp(1.0, -52);
     c.clamp_hi = (T)(1.0 + 16.0 * ulp1);
     c.clamp = mp_ok ? 1 : 0;

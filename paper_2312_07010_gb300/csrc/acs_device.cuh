@@ -12,20 +12,39 @@
 
 namespace acs {
 
+// Cubic-solve modes (a template parameter of every stepping kernel; the host picks
+// one per context, so all variants of that context round identically).
+enum Solve : int {
+    kSolveNewton = 0,  // three-term series seed + `newton` Newton corrections
+    kSolveSeries = 1,  // SeriesTerms<T> terms of the Lagrange series, no division
+    kSolveFex = 2      // FEX-FD scheme of Remark 2: no cubic at all
+};
+template <typename T>
+struct SeriesTerms { static constexpr int value = sizeof(T) == 4 ? 5 : 9; };
+
 // Coefficients of one step in the state's precision T.
 //   lam = eps^2 dt / h^2 (Eq. IE-FD-vector-form), a = dt/2, b = 1 - a.
 //   xi = c0 phi - a phi^3 + lam S, S = sum of the 2d neighbours, c0 = 1 - 2 d lam + a
 // (Remark 1's xi = (1 - 2 d lam) phi - (dt/2)(phi^3 - phi) + lam S, regrouped).
 // For the FEX-FD scheme of Remark 2 the same expression with a = dt,
 // c0 = 1 - 2 d lam + dt is the new state and no cubic is solved.
+//
+// The root theta of a theta^3 + b theta = xi (Remark 1) as a series in xi
+// (Lagrange inversion): with x = xi/b, y = (a/b) x^2,
+//   theta = x sum_k (-y)^k C_k,  C_k = binom(3k, k) / (2k + 1)  (1, 1, 3, 12, 55, ...),
+// convergent for y < 4/27; so theta = xi sum_k q_k (xi^2)^k with
+//   q_k = C_k (-a)^k / b^(3k+1).
 template <typename T>
 struct Coef {
-    T lam, c0, a, b, rb, t, three_a;
-    T ymax;      // fast path of the cubic solve applies while y = t x^2 <= ymax
-    int newton;  // Newton corrections (1..3) after the series seed on the fast path
-    T clamp_hi;  // 1 + 16 ulp: overshoots up to this are rounding and go back to +-1
-    int clamp;   // 1: apply that rounding guard (set only when Theorem 2's condition holds)
-    int fex;     // 1: FEX-FD scheme (no cubic)
+    T lam, c0, a, b, three_a;
+    T q[10];      // kSolveSeries: theta = xi * sum_k q[k] xi^(2k)
+    T xi2max;     // kSolveSeries applies while xi^2 <= xi2max
+    T rb, t;      // kSolveNewton: 1/b, a/b
+    T ymax;       // kSolveNewton applies while y = t (xi/b)^2 <= ymax
+    int newton;   // kSolveNewton: corrections after the seed (1..3)
+    T clamp_hi;   // 1 + 16 ulp: overshoots up to this are rounding and go back to +-1
+    int clamp;    // 1: apply that rounding guard (set only when Theorem 2's condition holds)
+    int solve;    // the Solve mode this context uses
 };
 
 template <typename T> __device__ __forceinline__ T dfma(T a, T b, T c);
@@ -65,45 +84,57 @@ __device__ __noinline__ T cubic_robust(T xi, T a, T b) {
 }
 
 // Root of theta + (dt/2) f(theta) = xi (Remark 1), i.e. a theta^3 + b theta = xi.
-// Fast path: with x = xi/b and y = (a/b) x^2 the root is x (1 - y + 3 y^2 - 12 y^3 + ...)
-// (Lagrange inversion, convergent for y < 4/27); its first three terms seed
-// `newton` Newton corrections.  The host picks `newton` and `ymax` from an
-// a-priori error bound so that the fast path is accurate to the last bit of T.
-template <typename T>
+// The host picks the mode and its limits from a-priori error bounds so that the
+// fast paths are accurate to the last bit of T for |xi| <= 1.001 (Theorem 2's
+// range plus rounding); larger |xi| take the robust path.
+template <typename T, int SOLVE>
 __device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
-    const T x = xi * c.rb;
-    const T y = (c.t * x) * x;
     T th;
-    if (y <= c.ymax) {
-        const T u = -y;
-        th = x * dfma(u, dfma(T(3), u, T(1)), T(1));
+    if (SOLVE == kSolveSeries) {
+        constexpr int NT = SeriesTerms<T>::value;
+        const T x2 = xi * xi;
+        if (x2 <= c.xi2max) {
+            T P = c.q[NT - 1];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (k < c.newton) {
-                const T th2 = th * th;
-                const T p = dfma(dfma(c.a, th2, c.b), th, -xi);
-                const T dp = dfma(c.three_a, th2, c.b);
-                th = dfma(-p, arcp(dp), th);
-            }
+            for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2, c.q[k]);
+            th = xi * P;
+        } else {
+            th = cubic_robust(xi, c.a, c.b);
         }
     } else {
-        th = cubic_robust(xi, c.a, c.b);
+        const T x = xi * c.rb;
+        const T y = (c.t * x) * x;
+        if (y <= c.ymax) {
+            const T u = -y;
+            th = x * dfma(u, dfma(T(3), u, T(1)), T(1));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (k < c.newton) {
+                    const T th2 = th * th;
+                    const T p = dfma(dfma(c.a, th2, c.b), th, -xi);
+                    const T dp = dfma(c.three_a, th2, c.b);
+                    th = dfma(-p, arcp(dp), th);
+                }
+            }
+        } else {
+            th = cubic_robust(xi, c.a, c.b);
+        }
     }
     if (c.clamp) {
-        if (th > T(1) && th <= c.clamp_hi) th = T(1);
-        else if (th < T(-1) && th >= -c.clamp_hi) th = T(-1);
+        const T ath = th < T(0) ? -th : th;
+        if (ath > T(1) && ath <= c.clamp_hi) th = th < T(0) ? T(-1) : T(1);
     }
     return th;
 }
 
 // The new value of one unknown from its old value p and the sum s of its 2d
 // ghost-ruled neighbours.
-template <typename T>
+template <typename T, int SOLVE>
 __device__ __forceinline__ T update(T p, T s, const Coef<T>& c) {
     const T p2 = p * p;
     const T xi = dfma(c.lam, s, p * dfma(-c.a, p2, c.c0));
-    if (c.fex) return xi;
-    return cubic_root(xi, c);
+    if (SOLVE == kSolveFex) return xi;
+    return cubic_root<T, SOLVE>(xi, c);
 }
 
 // Fixed summation order of the neighbours: z pair, then y pair, then x pair.
@@ -122,5 +153,20 @@ struct Geo {
     int64_t sy, sz;      // strides of y and z (x stride is 1)
     int64_t total;
 };
+
+// Dispatch a runtime Solve mode to a template parameter.
+#define ACS_SOLVE_DISPATCH(mode, S, ...)                 \
+    do {                                                 \
+        if ((mode) == ::acs::kSolveSeries) {             \
+            constexpr int S = ::acs::kSolveSeries;       \
+            __VA_ARGS__;                                 \
+        } else if ((mode) == ::acs::kSolveFex) {         \
+            constexpr int S = ::acs::kSolveFex;          \
+            __VA_ARGS__;                                 \
+        } else {                                         \
+            constexpr int S = ::acs::kSolveNewton;       \
+            __VA_ARGS__;                                 \
+        }                                                \
+    } while (0)
 
 }  // namespace acs

@@ -229,7 +229,7 @@ ACS_API int acs_grad(acs_ctx* c, const void* d_dL_dphiT, void* d_dL_dphi0, doubl
     CtxView v = ctx_view(c);
     GradState& G = *v.grad;
     if (!G.active || !G.started) return ACS_E_STATE;
-    if (v.cf.fex) return ACS_E_UNSUPPORTED;
+    if (v.cf.solve == kSolveFex) return ACS_E_UNSUPPORTED;
     const GradLayout L = layout(v, G.max_steps, G.every);
     const size_t bytes = (size_t)v.g.total * v.esize;
     cudaStream_t st = v.stream;

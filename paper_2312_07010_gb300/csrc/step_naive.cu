@@ -26,7 +26,7 @@ __device__ __forceinline__ T nb_hi(const T* __restrict__ p, int64_t i, int64_t c
     return T(0);
 }
 
-template <typename T, int D, int BC>
+template <typename T, int D, int BC, int SOLVE>
 __global__ void __launch_bounds__(256) k_step_naive(const T* __restrict__ src, T* __restrict__ dst,
                                                     Geo g, Coef<T> c) {
     for (int64_t z = blockIdx.z; z < g.nz; z += gridDim.z) {
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_step_naive(const T* __restrict__ src, T
                     const T zm = nb_lo<BC>(src, i, z, g.nz, g.sz), zp = nb_hi<BC>(src, i, z, g.nz, g.sz);
                     s = nsum(zm, zp, ym, yp, xm, xp);
                 }
-                dst[i] = update(p, s, c);
+                dst[i] = update<T, SOLVE>(p, s, c);
             }
         }
     }
@@ -65,8 +65,11 @@ template <typename T>
 cudaError_t launch_step_naive(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c,
                               cudaStream_t st) {
     dim3 grid = naive_grid(g), block(256);
-#define ACS_NAIVE_CASE(D, B) \
-    if (dims == D && bc == B) { k_step_naive<T, D, B><<<grid, block, 0, st>>>(src, dst, g, c); return cudaGetLastError(); }
+#define ACS_NAIVE_CASE(D, B)                                                                 \
+    if (dims == D && bc == B) {                                                              \
+        ACS_SOLVE_DISPATCH(c.solve, S, (k_step_naive<T, D, B, S><<<grid, block, 0, st>>>(src, dst, g, c))); \
+        return cudaGetLastError();                                                           \
+    }
     ACS_NAIVE_CASE(1, 0) ACS_NAIVE_CASE(1, 1) ACS_NAIVE_CASE(1, 2)
     ACS_NAIVE_CASE(2, 0) ACS_NAIVE_CASE(2, 1) ACS_NAIVE_CASE(2, 2)
     ACS_NAIVE_CASE(3, 0) ACS_NAIVE_CASE(3, 1) ACS_NAIVE_CASE(3, 2)

@@ -137,22 +137,23 @@ def test_fex_scheme_parity(acs, bc):
 
 
 def test_large_dt_robust_cubic(acs):
-    """Fig. 3(b): dt = 1/5 (lambda = 3.28) violates Theorem 2; |phi| exceeds 1 and the
-    robust cubic path must still match the oracle."""
+    """Fig. 3(b): dt = 1/5 (lambda = 3.28) violates Theorem 2 and |phi| exceeds 1, so the
+    cubic takes the robust path.  The run is violently unstable (rounding differences
+    grow by orders of magnitude per step), so each step starts from the oracle's state
+    and one step is compared."""
     h = 1 / 64
     eps = 8 * math.tanh(0.9) * h / math.sqrt(2)
     N = round(3 / h)
     x = -0.5 + h * np.arange(N + 1)
-    phi0 = 0.5 * (1 - np.tanh(x / (2 * math.sqrt(2) * eps)))
+    phi = 0.5 * (1 - np.tanh(x / (2 * math.sqrt(2) * eps)))
     s = acs.AllenCahn((N + 1,), eps, 0.2, h, BC_NEUMANN, "f64")
     assert s.create_status == 2
-    s.set_state(phi0)
-    ref = phi0
     worst = 0.0
-    for _ in range(6):
+    for _ in range(8):
+        s.set_state(phi)
         s.step(1)
-        ref = oracle.step_fd(ref, eps, 0.2, h, BC_NEUMANN)
-        assert relerr(s.numpy(), ref) <= 1e-12
+        phi = oracle.step_fd(phi, eps, 0.2, h, BC_NEUMANN)
+        assert relerr(s.numpy(), phi) <= 1e-13
         worst = max(worst, s.maxnorm(allow_nonfinite=True))
     assert worst > 1.0
 
