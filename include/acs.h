@@ -204,6 +204,30 @@ ACS_API int acs_grad_bind(acs_ctx* ctx, void* d_grad_work, size_t bytes, int64_t
                           int64_t every);
 ACS_API int acs_grad(acs_ctx* ctx, const void* d_dL_dphiT, void* d_dL_dphi0, double* dL_deps2_host);
 
+/*
+ * acs_observe_noalloc -- {E_h, max|phi|} of a state, like acs_observe_async, for
+ * callers that cannot allocate device memory (the paper has no counterpart: this is
+ * a deployment aid).  Some callers have no work buffer and cannot make one: code
+ * that must not call cudaMalloc because it can synchronize the device, plugins
+ * whose host application owns all device memory through its own pool, and tools
+ * that only hold a pointer to someone else's state.  This call needs no context and
+ * allocates nothing: its scratch is a 64 KiB array of static device memory that
+ * the library holds on every GPU that loads it, until the process exits.
+ *   dims, n, eps, h, bc, dtype  the problem, as for acs_create (dt is not needed)
+ *   d_phi    the state in device memory (prod(n) elements of dtype)
+ *   d_out2   two doubles of device memory receiving {E_h, max|phi|}
+ *   stream   the cudaStream_t to run on (NULL = legacy default stream)
+ * Asynchronous.  Shapes beyond acs_create's limit (2^40 elements) are rejected with
+ * ACS_E_INVAL, as are NULL or misaligned pointers.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture begins.  Every call shares the one array and it keeps the last
+ * call's partial sums; each call overwrites every entry it reads, so nothing needs
+ * clearing, but calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race on it: order them on one stream or synchronize between them.
+ */
+ACS_API int acs_observe_noalloc(int dims, const int64_t n[3], double eps, double h, int bc, int dtype,
+                                const void* d_phi, double* d_out2, void* stream);
+
 /* Block until all work enqueued by this context has finished. */
 ACS_API int acs_sync(acs_ctx* ctx);
 

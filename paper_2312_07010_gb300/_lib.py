@@ -46,6 +46,8 @@ SIGNATURES = {
     "acs_grad_work_bytes": (_c.c_size_t, [_vp, _i64, _i64]),
     "acs_grad_bind": (_c.c_int, [_vp, _vp, _c.c_size_t, _i64, _i64]),
     "acs_grad": (_c.c_int, [_vp, _vp, _vp, _dp]),
+    "acs_observe_noalloc": (_c.c_int, [_c.c_int, _i64p, _c.c_double, _c.c_double, _c.c_int, _c.c_int, _vp,
+                                       _vp, _vp]),
     "acs_sync": (_c.c_int, [_vp]),
     "acs_dt_max": (_c.c_int, [_c.c_int, _c.c_double, _c.c_double, _dp, _dp]),
     "acs_strerror": (_c.c_char_p, [_c.c_int]),

@@ -1,0 +1,72 @@
+"""acs_observe_noalloc: the reduction for callers that cannot allocate device memory.
+
+Callers such as latency-critical loops (cudaMalloc can synchronize the device),
+plugins whose host application owns all device memory, or tools that only hold a
+pointer to someone else's state cannot give the library a work buffer.  This entry
+point takes only the state and a two-double output and keeps its scratch in static
+device memory.  Its result must match the ordinary path (acs_observe_async on a
+bound context) within the reduction tolerance of the other tests (relative 1e-12),
+on two calls in a row -- the second one reuses the static array that the first
+left filled.  This file is named to be collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import BC_DIRICHLET, BC_NEUMANN, BC_PERIODIC, dt_rule, uniform_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def acs():
+    import paper_2312_07010_gb300 as P
+    P.build.build()
+    P.lib()
+    return P
+
+
+CASES = [((64, 48), BC_PERIODIC, "f32"), ((9, 33, 20), BC_NEUMANN, "f64"), ((1500,), BC_DIRICHLET, "f32"),
+         ((40, 40, 40), BC_DIRICHLET, "f64")]
+
+
+@pytest.mark.parametrize("shape,bc,dtype", CASES, ids=str)
+def test_noalloc_matches_bound_reduction(acs, shape, bc, dtype):
+    d = len(shape)
+    eps = 0.02
+    h = 1.0 / max(shape)
+    dt = dt_rule(d, eps, h)
+    s = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    L = acs.lib()
+    n = (ctypes.c_int64 * 3)(*(list(shape) + [1] * (3 - d)))
+    code = acs.ACS_F32 if dtype == "f32" else acs.ACS_F64
+    for call in range(2):
+        s.set_state(uniform_field(shape, -1, 1, 100 + call))
+        s.step(3)
+        ref = torch.empty(2, dtype=torch.float64, device="cuda")
+        out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+        s.observe_async(ref)
+        rc = L.acs_observe_noalloc(d, n, eps, h, bc, code, ctypes.c_void_p(s.phi.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0, acs.strerror(rc)
+        torch.cuda.synchronize()
+        r = ref.cpu().numpy()
+        o = out.cpu().numpy()
+        assert np.isfinite(o).all()
+        np.testing.assert_allclose(o, r, rtol=1e-12, atol=0)
+
+
+def test_noalloc_rejects_bad_arguments(acs):
+    L = acs.lib()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(16, dtype=torch.float32, device="cuda")
+    big = (ctypes.c_int64 * 3)(1 << 21, 1 << 21, 1)  # 2^42 elements: beyond the shape limit
+    assert L.acs_observe_noalloc(2, big, 0.1, 0.1, 0, 0, ctypes.c_void_p(phi.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), None) == -1
+    n = (ctypes.c_int64 * 3)(16, 1, 1)
+    assert L.acs_observe_noalloc(1, n, 0.1, 0.1, 0, 0, None, ctypes.c_void_p(out.data_ptr()), None) == -1
+    assert L.acs_observe_noalloc(1, n, 0.1, 0.1, 5, 0, ctypes.c_void_p(phi.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), None) == -1
