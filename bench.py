@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kernel", type=int, default=0, help="ACS_KERNEL_* (0 = auto)")
     ap.add_argument("--depth", type=int, default=1)
+    ap.add_argument("--profile", action="store_true",
+                    help="only set up the 512^3 workload and run --steps time steps (for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -237,6 +239,12 @@ def main():
     if args.kernel:
         s.set_kernel(args.kernel, args.depth)
     kernel, depth = s.get_kernel()
+    if args.profile:
+        s.set_state(phi0_dev)
+        s.step(args.steps)
+        s.sync()
+        print(json.dumps({"profile": True, "kernel": kernel, "depth": depth, "time_steps": args.steps}))
+        return 0
     log_every = 50
     n_logs = w.steps // log_every + 1
 

@@ -265,6 +265,12 @@ ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_
 ACS_API int acs_batch_step(acs_batch* b, int64_t n_steps);
 /* Per-instance E_h and max|phi| into host arrays of `count` doubles; synchronizes. */
 ACS_API int acs_batch_observe(acs_batch* b, double* h_energy, double* h_maxnorm);
+/* Testing aid for the failure path: mode 1 makes one CTA of the next batched launch
+ * skip its arrival at the first step barrier, so the other CTAs' bounded waits
+ * (about one second) expire, the launch ends early, and the next acs_batch_observe
+ * returns ACS_E_TIMEOUT (which also clears the fault state); mode 0 disarms it.  No
+ * GPU fault is involved. */
+ACS_API int acs_batch_inject_fault(acs_batch* b, int mode);
 ACS_API void acs_batch_destroy(acs_batch* b);
 
 #ifdef __cplusplus

@@ -61,6 +61,7 @@ SIGNATURES = {
     "acs_batch_bind": (_c.c_int, [_vp, _vp, _vp, _c.c_size_t, _vp]),
     "acs_batch_step": (_c.c_int, [_vp, _i64]),
     "acs_batch_observe": (_c.c_int, [_vp, _dp, _dp]),
+    "acs_batch_inject_fault": (_c.c_int, [_vp, _c.c_int]),
     "acs_batch_destroy": (None, [_vp]),
 }
 

@@ -153,6 +153,8 @@ struct acs_ctx {
     RedPartial* partials;
     double* result;
     double* log;
+    int* err;          // set by kernels whose bounded waits gave up
+    int zchunk;        // z planes per CTA of the 3D tiled kernel (0: default)
     int64_t steps_done;
     std::vector<GraphEntry> graphs;
     // adjoint recording
@@ -171,7 +173,8 @@ size_t state_bytes(const acs_ctx* c) { return (size_t)c->g.total * c->esize; }
 size_t off_partials(const acs_ctx* c) { return align_up(state_bytes(c)); }
 size_t off_result(const acs_ctx* c) { return off_partials(c) + align_up(sizeof(RedPartial) * kMaxRedBlocks); }
 size_t off_log(const acs_ctx* c) { return off_result(c) + kAlign; }
-size_t work_total(const acs_ctx* c) { return off_log(c) + align_up(sizeof(double) * 2 * kLogCap); }
+size_t off_flags(const acs_ctx* c) { return off_log(c) + align_up(sizeof(double) * 2 * kLogCap); }
+size_t work_total(const acs_ctx* c) { return off_flags(c) + kAlign; }
 
 void drop_graphs(acs_ctx* c) {
     for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
@@ -190,14 +193,18 @@ static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaS
     if (c->dtype == ACS_F32) {
         const float* s = (const float*)src;
         float* d = (float*)dst;
-        if (c->kernel == ACS_KERNEL_TEMPORAL) return launch_step_temporal<float>(c->dims, c->bc, k, s, d, c->g, c->cf, st);
-        if (c->kernel == ACS_KERNEL_TILED) return launch_step_tiled<float>(c->dims, c->bc, s, d, c->g, c->cf, st);
+        if (c->kernel == ACS_KERNEL_TEMPORAL)
+            return launch_step_temporal<float>(c->dims, c->bc, k, s, d, c->g, c->cf, c->err, st);
+        if (c->kernel == ACS_KERNEL_TILED)
+            return launch_step_tiled<float>(c->dims, c->bc, s, d, c->g, c->cf, c->zchunk, c->err, st);
         return launch_step_naive<float>(c->dims, c->bc, s, d, c->g, c->cf, st);
     }
     const double* s = (const double*)src;
     double* d = (double*)dst;
-    if (c->kernel == ACS_KERNEL_TEMPORAL) return launch_step_temporal<double>(c->dims, c->bc, k, s, d, c->g, c->cd, st);
-    if (c->kernel == ACS_KERNEL_TILED) return launch_step_tiled<double>(c->dims, c->bc, s, d, c->g, c->cd, st);
+    if (c->kernel == ACS_KERNEL_TEMPORAL)
+        return launch_step_temporal<double>(c->dims, c->bc, k, s, d, c->g, c->cd, c->err, st);
+    if (c->kernel == ACS_KERNEL_TILED)
+        return launch_step_tiled<double>(c->dims, c->bc, s, d, c->g, c->cd, c->zchunk, c->err, st);
     return launch_step_naive<double>(c->dims, c->bc, s, d, c->g, c->cd, st);
 }
 
@@ -274,6 +281,15 @@ static int run_steps(acs_ctx* c, int64_t n) {
     if (cudaGraphLaunch(hit->exec, c->stream) != cudaSuccess) return ACS_E_CUDA;
     c->steps_done += n;
     return ACS_OK;
+}
+
+// After a stream synchronization: report (and clear) a timeout recorded by a kernel.
+static int check_err_flag(acs_ctx* c) {
+    int h = 0;
+    if (cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_E_CUDA;
+    if (!h) return ACS_OK;
+    cudaMemset(c->err, 0, sizeof(int));
+    return ACS_E_TIMEOUT;
 }
 
 static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, cudaStream_t st) {
@@ -371,6 +387,8 @@ ACS_API int acs_create(int dims, const int64_t n[3], double eps, double dt, doub
     c->phi = nullptr; c->work = nullptr; c->work_bytes = 0;
     c->stream = nullptr; c->cap = nullptr;
     c->steps_done = 0;
+    c->err = nullptr;
+    c->zchunk = 0;
     c->grad = GradState();
     resolve_auto_kernel(c->dims, c->dtype, c->bc, c->g, &c->kernel, &c->depth);
     *out = c;
@@ -397,6 +415,8 @@ ACS_API int acs_bind(acs_ctx* c, void* d_phi, void* d_work, size_t work_bytes, v
     c->partials = (RedPartial*)(c->work + off_partials(c));
     c->result = (double*)(c->work + off_result(c));
     c->log = (double*)(c->work + off_log(c));
+    c->err = (int*)(c->work + off_flags(c));
+    if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) return ACS_E_CUDA;
     c->steps_done = 0;
     c->bound = true;
     return ACS_OK;
@@ -473,7 +493,8 @@ ACS_API int acs_get_state_host(acs_ctx* c, void* h_phi) {
     if (!c->bound) return ACS_E_STATE;
     if (cudaMemcpyAsync(h_phi, c->phi, state_bytes(c), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return ACS_E_CUDA;
-    return cudaStreamSynchronize(c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;
+    return check_err_flag(c);
 }
 
 ACS_API int acs_step(acs_ctx* c, int64_t n_steps) {
@@ -497,6 +518,7 @@ static int observe_host(acs_ctx* c, double* e, double* m) {
     if (cudaMemcpyAsync(hbuf, c->result, sizeof(hbuf), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return ACS_E_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;
+    if (int rc = check_err_flag(c)) return rc;
     if (e) *e = hbuf[0];
     if (m) *m = hbuf[1];
     const double v = e ? hbuf[0] : hbuf[1];
@@ -538,6 +560,7 @@ ACS_API int acs_run_logged(acs_ctx* c, int64_t n_steps, int64_t every, double* h
         cudaSuccess)
         return ACS_E_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;
+    if (int rc = check_err_flag(c)) return rc;
     bool finite = true;
     for (int64_t k = 0; k < entries; ++k) {
         h_energy[k] = buf[2 * k];
@@ -550,7 +573,8 @@ ACS_API int acs_run_logged(acs_ctx* c, int64_t n_steps, int64_t every, double* h
 ACS_API int acs_sync(acs_ctx* c) {
     if (!c) return ACS_E_INVAL;
     if (!c->bound) return ACS_OK;
-    return cudaStreamSynchronize(c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;
+    return check_err_flag(c);
 }
 
 ACS_API void acs_destroy(acs_ctx* c) {

@@ -47,6 +47,9 @@ struct Coef {
     int solve;    // the Solve mode this context uses
 };
 
+// 32-bit shared-memory address of a generic pointer into shared memory.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 template <typename T> __device__ __forceinline__ T dfma(T a, T b, T c);
 template <> __device__ __forceinline__ float dfma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <> __device__ __forceinline__ double dfma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -120,6 +123,28 @@ __device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
             th = cubic_robust(xi, c.a, c.b);
         }
     }
+    if (c.clamp) {
+        const T ath = th < T(0) ? -th : th;
+        if (ath > T(1) && ath <= c.clamp_hi) th = th < T(0) ? T(-1) : T(1);
+    }
+    return th;
+}
+
+// Pieces of update() for kernels that decide the cubic path once for several points:
+// the explicit predictor xi, the series root without its range check, the clamp.
+template <typename T>
+__device__ __forceinline__ T predictor(T p, T s, const Coef<T>& c) {
+    const T p2 = p * p;
+    return dfma(c.lam, s, p * dfma(-c.a, p2, c.c0));
+}
+template <typename T>
+__device__ __forceinline__ T series_root(T xi, const Coef<T>& c) {
+    constexpr int NT = SeriesTerms<T>::value;
+    const T x2 = xi * xi;
+    T P = c.q[NT - 1];
+#pragma unroll
+    for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2, c.q[k]);
+    T th = xi * P;
     if (c.clamp) {
         const T ath = th < T(0) ? -th : th;
         if (ath > T(1) && ath <= c.clamp_hi) th = th < T(0) ? T(-1) : T(1);

@@ -19,12 +19,13 @@ cudaError_t launch_step_naive(int dims, int bc, const T* src, T* dst, const Geo&
                               cudaStream_t st);
 
 // Tiled variants: return cudaErrorNotSupported when the shape is not covered.
+// err: device int set to 1 when a bounded wait inside the kernel gives up.
 template <typename T>
-cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c,
-                              cudaStream_t st);
+cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk,
+                              int* err, cudaStream_t st);
 template <typename T>
 cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* dst, const Geo& g,
-                                 const Coef<T>& c, cudaStream_t st);
+                                 const Coef<T>& c, int* err, cudaStream_t st);
 bool tiled_supported(int dims, int dtype, const Geo& g);
 bool temporal_supported(int dims, int dtype, int depth, const Geo& g);
 

@@ -17,53 +17,139 @@
 
 namespace acs {
 
+// ---------------------------------------------------------------- FP32 states
+// FP64 arithmetic runs at 1/57 of the FP32 rate on this GPU, so the FP32 path forms
+// every term exactly with error-free FP32 transformations (the build uses
+// -fmad=false, so nothing below is contracted): the difference q - p of two floats
+// is an exact pair (TwoSum), its square and p^2 are exact pairs up to the
+// negligible lo^2 term (TwoProduct via fma), and terms are accumulated into an
+// unevaluated float pair (hi, lo).  All terms are non-negative, so the pair keeps
+// about 2^-46 relative accuracy; every 32 points it is flushed into the FP64
+// compensated sum.
+
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return F2{s, (a - (s - bb)) + (b - bb)};
+}
+
+// acc += x (x >= 0 given as an unevaluated pair)
+__device__ __forceinline__ void f2_acc(F2& acc, float xh, float xl) {
+    const F2 t = two_sum(acc.hi, xh);
+    acc.hi = t.hi;
+    acc.lo = (acc.lo + t.lo) + xl;
+}
+
+// the exact square of (q - p), accumulated
+__device__ __forceinline__ void link_sq(F2& acc, float q, float p) {
+    const F2 d = two_sum(q, -p);
+    const float sq = d.hi * d.hi;
+    const float sql = __fmaf_rn(d.hi, d.hi, -sq) + 2.0f * d.hi * d.lo;
+    f2_acc(acc, sq, sql);
+}
+
+__device__ __forceinline__ void flush(F2& acc, CSum& sum) {
+    cadd(sum, (double)acc.hi);
+    cadd(sum, (double)acc.lo);
+    acc = F2{0.0f, 0.0f};
+}
+
 template <int BC>
-__device__ __forceinline__ void axis_links(CSum& acc, double p, double up, int64_t c, int64_t n) {
-    // the link from this unknown to the next one along the axis (if any), and the
-    // Dirichlet link from the first unknown down to the boundary value
-    if (c < n - 1) {
+__device__ __forceinline__ void axis_links_f(F2& acc, float p, float up, int64_t c, int64_t n) {
+    if (c < n - 1 || BC == ACS_BC_PERIODIC) link_sq(acc, up, p);  // `up` is the wrap neighbour at the end
+    else if (BC == ACS_BC_DIRICHLET) link_sq(acc, 0.0f, p);
+    if (BC == ACS_BC_DIRICHLET && c == 0) link_sq(acc, 0.0f, p);
+}
+
+// ---------------------------------------------------------------- FP64 states
+template <int BC>
+__device__ __forceinline__ void axis_links_d(double& acc, double p, double up, int64_t c, int64_t n) {
+    if (c < n - 1 || BC == ACS_BC_PERIODIC) {
         const double d = up - p;
-        cadd(acc, d * d);
-    } else if (BC == ACS_BC_PERIODIC) {
-        const double d = up - p;  // `up` is the wrap-around neighbour here
-        cadd(acc, d * d);
+        acc = fma(d, d, acc);
     } else if (BC == ACS_BC_DIRICHLET) {
-        cadd(acc, p * p);
+        acc = fma(p, p, acc);
     }
-    if (BC == ACS_BC_DIRICHLET && c == 0) cadd(acc, p * p);
+    if (BC == ACS_BC_DIRICHLET && c == 0) acc = fma(p, p, acc);
 }
 
 template <typename T, int D, int BC>
 __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g, RedPartial* part) {
     CSum bulk{0.0, 0.0}, link{0.0, 0.0};
-    double mx = 0.0;
+    float mx = 0.0f;
+    double mxd = 0.0;
+    F2 fb{0.0f, 0.0f}, fl{0.0f, 0.0f};
+    double db = 0.0, dl = 0.0;
+    int pending = 0;
     const int64_t rows = g.ny * g.nz;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
         const int64_t z = r / g.ny, y = r - z * g.ny;
         const int64_t row = z * g.sz + y * g.sy;
         for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) {
             const int64_t i = row + x;
-            const double p = (double)src[i];
-            const double w = p * p - 1.0;
-            cadd(bulk, 0.25 * w * w);
-            mx = nmax(mx, fabs(p));
-            axis_links<BC>(link, p, (double)src[x < g.nx - 1 ? i + 1 : row], x, g.nx);
-            if (D >= 2)
-                axis_links<BC>(link, p, (double)src[y < g.ny - 1 ? i + g.sy : z * g.sz + x], y, g.ny);
-            if (D >= 3)
-                axis_links<BC>(link, p, (double)src[z < g.nz - 1 ? i + g.sz : y * g.sy + x], z, g.nz);
+            const T p = src[i];
+            const T ux = src[x < g.nx - 1 ? i + 1 : row];
+            const T uy = D >= 2 ? src[y < g.ny - 1 ? i + g.sy : z * g.sz + x] : T(0);
+            const T uz = D >= 3 ? src[z < g.nz - 1 ? i + g.sz : y * g.sy + x] : T(0);
+            if (sizeof(T) == 4) {
+                const float pf = (float)p;
+                // (p^2 - 1)^2 exactly up to 2^-46: p^2 = s + sl, w = p^2 - 1 = wh + wl
+                const float s2 = pf * pf;
+                const float s2l = __fmaf_rn(pf, pf, -s2);
+                const F2 w = two_sum(s2, -1.0f);
+                const float wh = w.hi, wl = w.lo + s2l;
+                const float q = wh * wh;
+                const float ql = __fmaf_rn(wh, wh, -q) + 2.0f * wh * wl;
+                f2_acc(fb, q, ql);
+                const float ap = fabsf(pf);
+                mx = (ap > mx || ap != ap) ? ap : mx;
+                axis_links_f<BC>(fl, pf, (float)ux, x, g.nx);
+                if (D >= 2) axis_links_f<BC>(fl, pf, (float)uy, y, g.ny);
+                if (D >= 3) axis_links_f<BC>(fl, pf, (float)uz, z, g.nz);
+                if (++pending == 32) {
+                    flush(fb, bulk);
+                    flush(fl, link);
+                    pending = 0;
+                }
+            } else {
+                const double pd = (double)p;
+                const double w = fma(pd, pd, -1.0);
+                db = fma(w, w, db);
+                mxd = nmax(mxd, fabs(pd));
+                axis_links_d<BC>(dl, pd, (double)ux, x, g.nx);
+                if (D >= 2) axis_links_d<BC>(dl, pd, (double)uy, y, g.ny);
+                if (D >= 3) axis_links_d<BC>(dl, pd, (double)uz, z, g.nz);
+                if (++pending == 32) {
+                    cadd(bulk, db);
+                    cadd(link, dl);
+                    db = dl = 0.0;
+                    pending = 0;
+                }
+            }
         }
     }
-    // warp then block combination in a fixed order
+    if (sizeof(T) == 4) {
+        flush(fb, bulk);
+        flush(fl, link);
+        mxd = (double)mx;
+    } else {
+        cadd(bulk, db);
+        cadd(link, dl);
+    }
+    // the bulk terms above are (p^2 - 1)^2; the 1/4 is applied at the end (exact)
     for (int off = 16; off > 0; off >>= 1) {
         bulk = cmerge(bulk, shfl_down(bulk, off));
         link = cmerge(link, shfl_down(link, off));
-        mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+        mxd = nmax(mxd, __shfl_down_sync(0xffffffffu, mxd, off));
     }
     __shared__ CSum sb[8], sl[8];
     __shared__ double sm[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sb[warp] = bulk; sl[warp] = link; sm[warp] = mx; }
+    if (lane == 0) { sb[warp] = bulk; sl[warp] = link; sm[warp] = mxd; }
     __syncthreads();
     if (threadIdx.x == 0) {
         CSum B = sb[0], L = sl[0];
@@ -96,7 +182,7 @@ __global__ void k_reduce_finish(const RedPartial* part, int nparts, double hd, d
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { sb[0] = cmerge(sb[0], sb[w]); sl[0] = cmerge(sl[0], sl[w]); sm[0] = nmax(sm[0], sm[w]); }
         const double bulk = sb[0].s + sb[0].c;
         const double links = sl[0].s + sl[0].c;
-        out2[0] = hd * (bulk + link_scale * links);
+        out2[0] = hd * (0.25 * bulk + link_scale * links);
         out2[1] = sm[0];
     }
 }

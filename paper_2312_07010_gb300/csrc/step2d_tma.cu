@@ -1,0 +1,216 @@
+// step2d_tma.cu -- one RLB-MIE-FD step (Eq. IE-FD, Remark 1) on a 2D grid whose rows
+// are a multiple of 16 bytes, streaming TMA-staged blocks of 16 rows.
+//
+// A CTA owns a column of TX unknowns (128 FP32 / 64 FP64) and a run of 16-row
+// blocks.  One thread issues a TMA load of each block plus a one-cell halo (rows
+// y0 - 1 .. y0 + 16, the x halo widened to a 16-byte group) into a 4-slot ring, up
+// to four blocks ahead; each of the 256 threads owns one 16-byte vector in two rows
+// and takes its x neighbours from its registers and warp shuffles, its y neighbours
+// from shared memory.  Boundaries as in the 3D kernel: TMA zero fill for Dirichlet,
+// per-row fix-ups (own value / wrapped global read) for Neumann and periodic.
+#include "acs_host.h"
+#include "stream_tile.cuh"
+#include "tma.cuh"
+
+namespace acs {
+
+template <typename T, int BC, int SOLVE>
+__global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUtensorMap tmap,
+                                                    const T* __restrict__ src, T* __restrict__ dst, Geo g,
+                                                    Coef<T> c, int ybchunk, int* err) {
+    using TT = Tile3<T>;
+    constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
+    constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base);
+    T* ring = reinterpret_cast<T*>(base + TT::BAR_BYTES);
+
+    const int nx = (int)g.nx, ny = (int)g.ny;
+    const int nyb = (ny + TY - 1) / TY;
+    const int x0 = blockIdx.x * TX;
+    const int b0 = blockIdx.y * ybchunk;
+    const int b1 = min(b0 + ybchunk, nyb);
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int tid = ly * 32 + lx;
+    const int xl = lx * VX;
+    const int gx = x0 + xl;
+    const int r0 = 2 * ly;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int b) {
+        const int k = b - b0;
+        T* dstp = ring + (size_t)(k % S) * SLOT_ELEMS;
+        if ((smem_u32(dstp) & 127u) != 0u || (((x0 - VX) * (int)sizeof(T)) & 15) != 0) {
+            atomicExch(err, 2);
+            return;
+        }
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[k % S], TT::SLOT_BYTES);
+        tma_load_2d(dstp, &tmap, &full[k % S], x0 - VX, b * TY - 1);
+    };
+    int last_issued = min(b0 + S, b1) - 1;
+    if (tid == 0)
+        for (int b = b0; b <= last_issued; ++b) issue(b);
+
+    const int64_t sy = g.sy;
+    const bool edge = BC != ACS_BC_DIRICHLET;  // Neumann / periodic fix-ups at the faces
+    const bool xlo = gx == 0, xhi = gx + VX == nx;
+    const bool vecok = gx + VX <= nx;
+    bool failed = false;
+    for (int b = b0; b < b1 && !failed; ++b) {
+        const int k = b - b0;
+        const bool ok = mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
+        const T* cur = ring + (size_t)(k % S) * SLOT_ELEMS;
+        const int gy0 = b * TY + r0;
+        T cz[2][VX], xi[2][VX];
+        Vec<T>::get(cur + (r0 + 1) * BW + VX + xl, cz[0]);
+        Vec<T>::get(cur + (r0 + 2) * BW + VX + xl, cz[1]);
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int gyr = gy0 + rr;
+            T ym[VX], yp[VX];
+            if (rr == 0) {
+                Vec<T>::get(cur + r0 * BW + VX + xl, ym);
+#pragma unroll
+                for (int v = 0; v < VX; ++v) yp[v] = cz[1][v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < VX; ++v) ym[v] = cz[0][v];
+                Vec<T>::get(cur + (r0 + 3) * BW + VX + xl, yp);
+            }
+            T left = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
+            T right = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
+            if (lx == 0) left = cur[(r0 + rr + 1) * BW + VX - 1];
+            if (lx == 31) right = cur[(r0 + rr + 1) * BW + VX + TX];
+            if (edge && gyr < ny) {
+                if (gyr == 0) {
+                    if (BC == ACS_BC_NEUMANN) {
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) ym[v] = cz[rr][v];
+                    } else if (gx < nx) {
+                        Vec<T>::ldg(src + (int64_t)(ny - 1) * sy + gx, ym);
+                    }
+                }
+                if (gyr == ny - 1) {
+                    if (BC == ACS_BC_NEUMANN) {
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) yp[v] = cz[rr][v];
+                    } else if (gx < nx) {
+                        Vec<T>::ldg(src + gx, yp);
+                    }
+                }
+                if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[(int64_t)gyr * sy + nx - 1];
+                if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[(int64_t)gyr * sy];
+            }
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                const T xm = v == 0 ? left : cz[rr][v - 1];
+                const T xp = v == VX - 1 ? right : cz[rr][v + 1];
+                xi[rr][v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
+            }
+        }
+        T out[2][VX];
+        bool fast = SOLVE == kSolveSeries;
+        if (SOLVE == kSolveSeries) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) fast = fast && (xi[rr][v] * xi[rr][v] <= c.xi2max);
+        }
+        if (fast) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) out[rr][v] = series_root(xi[rr][v], c);
+        } else if (SOLVE == kSolveFex) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) out[rr][v] = xi[rr][v];
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) out[rr][v] = cubic_root<T, SOLVE>(xi[rr][v], c);
+        }
+        T* o = dst + (int64_t)gy0 * sy + gx;
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            if (gy0 + rr >= ny) continue;
+            if (vecok) {
+                Vec<T>::put(o + rr * sy, out[rr]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VX; ++v)
+                    if (gx + v < nx) o[rr * sy + v] = out[rr][v];
+            }
+        }
+        failed = __syncthreads_or(!ok);
+        if (!failed && tid == 0 && b + S < b1) {
+            issue(b + S);
+            last_issued = b + S;
+        }
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int b = max(b0, last_issued - S + 1); b <= last_issued; ++b) {
+                const int k = b - b0;
+                mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+bool step2d_tma_supported(int dtype, const Geo& g) {
+    const int esize = dtype == ACS_F32 ? 4 : 8;
+    return g.nz == 1 && (g.nx * esize) % 16 == 0 && g.nx < (1 << 30) && g.ny < (1 << 30);
+}
+
+template <typename T>
+cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ybchunk, int* err,
+                              cudaStream_t st) {
+    using TT = Tile3<T>;
+    CUtensorMap map;
+    const uint64_t dims[2] = {(uint64_t)g.nx, (uint64_t)g.ny};
+    const uint32_t box[2] = {(uint32_t)TT::BW, (uint32_t)TT::BH};
+    if (!encode_tensor_map(&map, sizeof(T), 2, src, dims, box)) return cudaErrorNotSupported;
+    const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX);
+    const int nyb = (int)((g.ny + TT::TY - 1) / TT::TY);
+    if (ybchunk <= 0) {
+        // about eight CTAs per SM over the launch, at least four blocks each
+        const int want = 152 * 8;
+        const int chunks = std::max(1, std::min(nyb / 4 > 0 ? nyb / 4 : 1, (want + ntx - 1) / ntx));
+        ybchunk = (nyb + chunks - 1) / chunks;
+    }
+    const int nchunks = (nyb + ybchunk - 1) / ybchunk;
+    if (nchunks > 65535) return cudaErrorNotSupported;
+    dim3 grid((unsigned)ntx, (unsigned)nchunks), block(32, 8);
+    cudaError_t e = cudaSuccess;
+#define ACS_2DT_CASE(B)                                                                                  \
+    if (bc == B) {                                                                                       \
+        ACS_SOLVE_DISPATCH(c.solve, SV, {                                                                \
+            auto kern = k_step2d_tma<T, B, SV>;                                                          \
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);  \
+            if (e == cudaSuccess) kern<<<grid, block, TT::SMEM, st>>>(map, src, dst, g, c, ybchunk, err); \
+        });                                                                                              \
+    }
+    ACS_2DT_CASE(0) ACS_2DT_CASE(1) ACS_2DT_CASE(2)
+#undef ACS_2DT_CASE
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step2d_tma<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int*,
+                                              cudaStream_t);
+template cudaError_t launch_step2d_tma<double>(int, const double*, double*, const Geo&, const Coef<double>&, int,
+                                               int*, cudaStream_t);
+
+}  // namespace acs

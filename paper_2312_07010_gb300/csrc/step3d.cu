@@ -1,0 +1,296 @@
+// step3d.cu -- one RLB-MIE-FD step (Eq. IE-FD, Remark 1) on a 3D grid, streaming
+// through z with TMA-staged xy planes.
+//
+// A CTA owns an xy tile of TX x TY unknowns (TX = 128 FP32 / 64 FP64, TY = 16) and a
+// chunk of z.  One thread issues TMA loads of each z plane's tile plus a one-cell
+// halo (the x halo widened to a 16-byte group so every box starts on a 16-byte
+// boundary) into a ring of S shared-memory slots, S - 2 planes ahead of the
+// compute.  Each of the 256 threads owns VX consecutive x (one 16-byte vector) in
+// two rows: its z-1 and z values stay in registers, z+1 and the y neighbours come
+// from shared memory, the x neighbours from its own registers and warp shuffles.
+// Every unknown is read from HBM once per step and written once.
+//
+// Boundaries: along z the producer loads the plane the ghost rule names (wrapped for
+// periodic, the edge plane itself for Neumann, an out-of-range plane -- TMA zero fill
+// -- for Dirichlet).  Along x and y the zero fill gives Dirichlet; Neumann uses the
+// point's own value and periodic reads the wrapped neighbour from global memory.
+#include "acs_host.h"
+#include "stream_tile.cuh"
+#include "tma.cuh"
+
+namespace acs {
+
+template <typename T, int BC, int SOLVE>
+__global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src,
+                                                T* __restrict__ dst, Geo g, Coef<T> c, int ntx, int zchunk,
+                                                int* err) {
+    using TT = Tile3<T>;
+    constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
+    constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // align the ring to 128 bytes whatever the base alignment of dynamic shared memory
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base);
+    T* ring = reinterpret_cast<T*>(base + TT::BAR_BYTES);
+
+    const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+    const int z0 = blockIdx.y * zchunk;
+    const int z1 = min(z0 + zchunk, nz);
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int tid = ly * 32 + lx;
+    const int xl = lx * VX;
+    const int gx = x0 + xl;
+    const int r0 = 2 * ly;
+    const int gy[2] = {y0 + r0, y0 + r0 + 1};
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int p) {
+        const int k = p - (z0 - 1);
+        const int s = k % S;
+        T* dstp = ring + (size_t)s * SLOT_ELEMS;
+        // self-check of the TMA preconditions: a misaligned destination or x offset is
+        // recorded and the copy skipped (the consumers' bounded wait then reports it)
+        if ((smem_u32(dstp) & 127u) != 0u || (((x0 - VX) * (int)sizeof(T)) & 15) != 0) {
+            atomicExch(err, 2);
+            return;
+        }
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[s], TT::SLOT_BYTES);
+        tma_load_3d(dstp, &tmap, &full[s], x0 - VX, y0 - 1, zsrc<BC>(p, nz));
+    };
+    auto slot_of = [&](int p) { return ring + (size_t)((p - (z0 - 1)) % S) * SLOT_ELEMS; };
+    auto wait_plane = [&](int p) -> bool {
+        const int k = p - (z0 - 1);
+        return mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
+    };
+    // my two rows x VX values of a plane, from shared memory
+    auto read_mine = [&](const T* sl, T (&o)[2][VX]) {
+        Vec<T>::get(sl + (r0 + 1) * BW + VX + xl, o[0]);
+        Vec<T>::get(sl + (r0 + 2) * BW + VX + xl, o[1]);
+    };
+
+    int last_issued = z0 - 2;
+    if (tid == 0) {
+        for (int p = z0 - 1; p <= min(z0 + S - 2, z1); ++p) issue(p);
+    }
+    last_issued = min(z0 + S - 2, z1);
+
+    T zm[2][VX], cz[2][VX];
+    bool ok = wait_plane(z0 - 1);
+    read_mine(slot_of(z0 - 1), zm);
+    ok = wait_plane(z0) && ok;
+    read_mine(slot_of(z0), cz);
+    bool failed = __syncthreads_or(!ok);
+    if (!failed && tid == 0 && z0 + S - 1 <= z1) issue(z0 + S - 1);
+    last_issued = failed ? last_issued : min(z0 + S - 1, z1);
+
+    const int64_t sy = g.sy, sz = g.sz;
+    // Boundary handling hoisted out of the z loop.  Only a CTA whose tile touches an
+    // x or y face (Neumann / periodic) takes the per-row fix-ups; Dirichlet needs none
+    // (TMA zero fill), and z faces are handled by the producer's plane choice.
+    const bool edge = BC != ACS_BC_DIRICHLET && (x0 == 0 || x0 + TX >= nx || y0 == 0 || y0 + TY >= ny);
+    const bool xlo = gx == 0, xhi = gx + VX == nx;
+    const bool rowok0 = gy[0] < ny, rowok1 = gy[1] < ny;
+    const bool vecok = gx + VX <= nx;
+    T* o = dst + (int64_t)z0 * sz + (int64_t)gy[0] * sy + gx;
+
+    // One plane: zm / cz / zp are this thread's values at z-1, z, z+1.
+    auto plane = [&](int z, T (&zm)[2][VX], T (&cz)[2][VX], T (&zp)[2][VX]) {
+        ok = wait_plane(z + 1);
+        read_mine(slot_of(z + 1), zp);
+        const T* cur = slot_of(z);
+        T xi[2][VX];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int r = r0 + rr;
+            T ym[VX], yp[VX];
+            if (rr == 0) {
+                Vec<T>::get(cur + r * BW + VX + xl, ym);  // row r - 1 (box row r)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) yp[v] = cz[1][v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < VX; ++v) ym[v] = cz[0][v];
+                Vec<T>::get(cur + (r + 2) * BW + VX + xl, yp);  // row r + 1 (box row r + 2)
+            }
+            // x neighbours across lanes; the tile's outer two come from the halo group
+            T left = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
+            T right = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
+            if (lx == 0) left = cur[(r + 1) * BW + VX - 1];
+            if (lx == 31) right = cur[(r + 1) * BW + VX + TX];
+            if (edge && (rr == 0 ? rowok0 : rowok1)) {
+                const int gyr = gy[rr];
+                const int64_t rowoff = (int64_t)z * sz + (int64_t)gyr * sy;
+                if (gyr == 0) {
+                    if (BC == ACS_BC_NEUMANN) {
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) ym[v] = cz[rr][v];
+                    } else if (gx < nx) {
+                        Vec<T>::ldg(src + (int64_t)z * sz + (int64_t)(ny - 1) * sy + gx, ym);
+                    }
+                }
+                if (gyr == ny - 1) {
+                    if (BC == ACS_BC_NEUMANN) {
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) yp[v] = cz[rr][v];
+                    } else if (gx < nx) {
+                        Vec<T>::ldg(src + (int64_t)z * sz + gx, yp);
+                    }
+                }
+                if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[rowoff + nx - 1];
+                if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[rowoff];
+            }
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                const T xm = v == 0 ? left : cz[rr][v - 1];
+                const T xp = v == VX - 1 ? right : cz[rr][v + 1];
+                const T s = nsum(zm[rr][v], zp[rr][v], ym[v], yp[v], xm, xp);
+                xi[rr][v] = predictor(cz[rr][v], s, c);
+            }
+        }
+        // one decision per thread for the cubic path of its 2 x VX points
+        T out[2][VX];
+        bool fast = SOLVE == kSolveSeries;
+        if (SOLVE == kSolveSeries) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) fast = fast && (xi[rr][v] * xi[rr][v] <= c.xi2max);
+        }
+        if (fast) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) out[rr][v] = series_root(xi[rr][v], c);
+        } else if (SOLVE == kSolveFex) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) out[rr][v] = xi[rr][v];
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) out[rr][v] = cubic_root<T, SOLVE>(xi[rr][v], c);
+        }
+        if (vecok) {
+            if (rowok0) Vec<T>::put(o, out[0]);
+            if (rowok1) Vec<T>::put(o + sy, out[1]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                if (gx + v < nx && rowok0) o[v] = out[0][v];
+                if (gx + v < nx && rowok1) o[sy + v] = out[1][v];
+            }
+        }
+        o += sz;
+        failed = __syncthreads_or(!ok);
+        if (!failed && tid == 0 && z + S <= z1) issue(z + S);
+        if (!failed) last_issued = max(last_issued, min(z + S, z1));
+    };
+
+    // the three register sets rotate roles, so the loop is unrolled by three
+    T zq[2][VX];
+    int z = z0;
+    for (; z + 3 <= z1 && !failed; z += 3) {
+        plane(z, zm, cz, zq);
+        if (failed) break;
+        plane(z + 1, cz, zq, zm);
+        if (failed) break;
+        plane(z + 2, zq, zm, cz);
+    }
+    if (!failed && z < z1) {
+        plane(z, zm, cz, zq);
+        if (!failed && z + 1 < z1) plane(z + 1, cz, zq, zm);
+    }
+    if (failed) {
+        // record the timeout, then let the newest load of every slot land (bounded)
+        // before the CTA's shared memory goes away
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int p = max(z0 - 1, last_issued - S + 1); p <= last_issued; ++p) {
+                const int k = p - (z0 - 1);
+                mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+bool step3d_supported(int dtype, const Geo& g) {
+    const int esize = dtype == ACS_F32 ? 4 : 8;
+    // TMA: row stride a multiple of 16 bytes; coordinates fit in int32
+    return g.nz >= 1 && (g.nx * esize) % 16 == 0 && g.nx < (1 << 30) && g.ny < (1 << 30) && g.nz < (1 << 30);
+}
+
+// z planes per CTA: minimize (waves of resident CTAs) x (planes per CTA + pipeline
+// fill), the launch's critical path; a chunk also re-reads its two halo planes.
+template <typename T>
+static int choose_zchunk(const Geo& g, int resident) {
+    using TT = Tile3<T>;
+    const int64_t tiles = ((g.nx + TT::TX - 1) / TT::TX) * ((g.ny + TT::TY - 1) / TT::TY);
+    const int64_t nz = g.nz;
+    int best = (int)nz;
+    double best_cost = 1e300;
+    for (int64_t zc = std::min<int64_t>(nz, 4); zc <= nz; ++zc) {
+        const int64_t chunks = (nz + zc - 1) / zc;
+        if (chunks > 65535) continue;
+        const int64_t waves = (tiles * chunks + resident - 1) / resident;
+        const double cost = (double)waves * (double)(zc + 3);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = (int)zc; }
+    }
+    return best;
+}
+
+template <typename T>
+cudaError_t launch_step3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk, int* err,
+                          cudaStream_t st) {
+    using TT = Tile3<T>;
+    CUtensorMap map;
+    const uint64_t dims[3] = {(uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz};
+    const uint32_t box[3] = {(uint32_t)TT::BW, (uint32_t)TT::BH, 1u};
+    if (!encode_tensor_map(&map, sizeof(T), 3, src, dims, box)) return cudaErrorNotSupported;
+    if (zchunk <= 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ACS_SOLVE_DISPATCH(c.solve, SV, {
+            auto kern = bc == 0 ? k_step3d<T, 0, SV> : (bc == 1 ? k_step3d<T, 1, SV> : k_step3d<T, 2, SV>);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, TT::SMEM);
+        });
+        zchunk = choose_zchunk<T>(g, std::max(1, sms * std::max(1, per_sm)));
+    }
+    const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX);
+    const int nty = (int)((g.ny + TT::TY - 1) / TT::TY);
+    const int nzc = (int)((g.nz + zchunk - 1) / zchunk);
+    if ((int64_t)ntx * nty > 0x7fffffff || nzc > 65535) return cudaErrorNotSupported;
+    dim3 grid((unsigned)(ntx * nty), (unsigned)nzc), block(32, 8);
+    cudaError_t e = cudaSuccess;
+#define ACS_3D_CASE(B)                                                                                   \
+    if (bc == B) {                                                                                       \
+        ACS_SOLVE_DISPATCH(c.solve, SV, {                                                                \
+            auto kern = k_step3d<T, B, SV>;                                                              \
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);  \
+            if (e == cudaSuccess) kern<<<grid, block, TT::SMEM, st>>>(map, src, dst, g, c, ntx, zchunk, err); \
+        });                                                                                              \
+    }
+    ACS_3D_CASE(0) ACS_3D_CASE(1) ACS_3D_CASE(2)
+#undef ACS_3D_CASE
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step3d<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int*,
+                                          cudaStream_t);
+template cudaError_t launch_step3d<double>(int, const double*, double*, const Geo&, const Coef<double>&, int, int*,
+                                           cudaStream_t);
+
+}  // namespace acs

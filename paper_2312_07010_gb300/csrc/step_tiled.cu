@@ -1,31 +1,96 @@
-// step_tiled.cu -- shared-memory tiled and temporally blocked step kernels.
+// step_tiled.cu -- selection and dispatch of the tiled / temporally blocked step
+// kernels, and tensor-map encoding for their TMA loads.
+#include <mutex>
+
 #include "acs_host.h"
+#include "tma.cuh"
 
 namespace acs {
 
-bool tiled_supported(int dims, int dtype, const Geo& g) { (void)dims; (void)dtype; (void)g; return false; }
+bool step3d_supported(int dtype, const Geo& g);
+template <typename T>
+cudaError_t launch_step3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk, int* err,
+                          cudaStream_t st);
+
+bool step2d_supported(const Geo& g);
+template <typename T>
+cudaError_t launch_step2d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int per_cta,
+                          cudaStream_t st);
+
+bool step2d_tma_supported(int dtype, const Geo& g);
+template <typename T>
+cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ybchunk, int* err,
+                              cudaStream_t st);
+
+bool encode_tensor_map(CUtensorMap* map, int esize, int rank, const void* base, const uint64_t* dims,
+                       const uint32_t* box) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    if (!fn || rank < 1 || rank > 5) return false;
+    cuuint64_t gd[5], gs[4];
+    cuuint32_t bx[5], es[5];
+    uint64_t stride = (uint64_t)esize;
+    for (int i = 0; i < rank; ++i) {
+        gd[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i > 0) gs[i - 1] = stride;
+        stride *= dims[i];
+    }
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool tiled_supported(int dims, int dtype, const Geo& g) {
+    if (dims == 3) return step3d_supported(dtype, g);
+    if (dims == 2) return step2d_supported(g);
+    return false;
+}
+
 bool temporal_supported(int dims, int dtype, int depth, const Geo& g) {
     (void)dims; (void)dtype; (void)depth; (void)g;
     return false;
 }
 
 template <typename T>
-cudaError_t launch_step_tiled(int, int, const T*, T*, const Geo&, const Coef<T>&, cudaStream_t) {
+cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk,
+                              int* err, cudaStream_t st) {
+    if (dims == 3) return launch_step3d<T>(bc, src, dst, g, c, zchunk, err, st);
+    if (dims == 2) {
+        if (step2d_tma_supported(sizeof(T) == 4 ? ACS_F32 : ACS_F64, g))
+            return launch_step2d_tma<T>(bc, src, dst, g, c, zchunk, err, st);
+        return launch_step2d<T>(bc, src, dst, g, c, zchunk, st);
+    }
     return cudaErrorNotSupported;
 }
 template <typename T>
-cudaError_t launch_step_temporal(int, int, int, const T*, T*, const Geo&, const Coef<T>&, cudaStream_t) {
+cudaError_t launch_step_temporal(int, int, int, const T*, T*, const Geo&, const Coef<T>&, int*, cudaStream_t) {
     return cudaErrorNotSupported;
 }
-template cudaError_t launch_step_tiled<float>(int, int, const float*, float*, const Geo&, const Coef<float>&, cudaStream_t);
-template cudaError_t launch_step_tiled<double>(int, int, const double*, double*, const Geo&, const Coef<double>&, cudaStream_t);
-template cudaError_t launch_step_temporal<float>(int, int, int, const float*, float*, const Geo&, const Coef<float>&, cudaStream_t);
-template cudaError_t launch_step_temporal<double>(int, int, int, const double*, double*, const Geo&, const Coef<double>&, cudaStream_t);
+template cudaError_t launch_step_tiled<float>(int, int, const float*, float*, const Geo&, const Coef<float>&, int,
+                                              int*, cudaStream_t);
+template cudaError_t launch_step_tiled<double>(int, int, const double*, double*, const Geo&, const Coef<double>&,
+                                               int, int*, cudaStream_t);
+template cudaError_t launch_step_temporal<float>(int, int, int, const float*, float*, const Geo&,
+                                                 const Coef<float>&, int*, cudaStream_t);
+template cudaError_t launch_step_temporal<double>(int, int, int, const double*, double*, const Geo&,
+                                                  const Coef<double>&, int*, cudaStream_t);
 
 void resolve_auto_kernel(int dims, int dtype, int bc, const Geo& g, int* kernel, int* depth) {
-    (void)dims; (void)dtype; (void)bc; (void)g;
-    *kernel = ACS_KERNEL_NAIVE;
+    (void)bc;
     *depth = 1;
+    *kernel = tiled_supported(dims, dtype, g) ? ACS_KERNEL_TILED : ACS_KERNEL_NAIVE;
 }
 
 }  // namespace acs

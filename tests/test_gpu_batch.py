@@ -1,0 +1,94 @@
+"""Batched stepping (acs_batch_*) on the GPU.
+
+Every instance of a batched launch must equal its standalone run bit for bit (same
+kernel arithmetic, same coefficients); FP64 instances also match the oracle within
+1e-12 relative; per-instance E_h / max-norm match the standalone reductions; and the
+bounded grid barrier turns an injected missing arrival into ACS_E_TIMEOUT.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import batched_instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def acs():
+    import paper_2312_07010_gb300 as P
+    P.build.build()
+    P.lib()
+    return P
+
+
+def _instances(count, seed, n_lo, n_hi):
+    return batched_instances(count=count, seed=seed, n_lo=n_lo, n_hi=n_hi)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 37])
+def test_batch_equals_standalone_fp32(acs, steps):
+    inst = _instances(24, 5, 8, 300)
+    b = acs.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+                  [i.bc for i in inst], "f32")
+    phi0 = [i.phi0().astype(np.float32) for i in inst]
+    b.set_states(phi0)
+    b.step(steps)
+    got = b.states()
+    E, M = b.observe()
+    for k, i in enumerate(inst):
+        s = acs.AllenCahn((i.n, i.n), i.eps, i.dt, i.h, i.bc, "f32")
+        s.set_state(phi0[k])
+        s.step(steps)
+        assert np.array_equal(got[k], s.numpy()), k
+        assert E[k] == s.energy() and M[k] == s.maxnorm()
+
+
+def test_batch_fp64_vs_oracle(acs):
+    inst = _instances(6, 9, 16, 200)
+    b = acs.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+                  [i.bc for i in inst], "f64")
+    phi0 = [i.phi0() for i in inst]
+    b.set_states(phi0)
+    b.step(20)
+    got = b.states()
+    for k, i in enumerate(inst):
+        ref = oracle.run_fd(phi0[k], i.eps, i.dt, i.h, i.bc, 20)
+        assert np.abs(got[k] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_batch_calls_compose(acs):
+    inst = _instances(10, 3, 30, 260)
+    args = ([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+            [i.bc for i in inst], "f32")
+    a = acs.Batch(*args)
+    b = acs.Batch(*args)
+    phi0 = [i.phi0().astype(np.float32) for i in inst]
+    a.set_states(phi0)
+    b.set_states(phi0)
+    a.step(12)
+    for _ in range(4):
+        b.step(3)
+    for x, y in zip(a.states(), b.states()):
+        assert np.array_equal(x, y)
+
+
+def test_batch_barrier_timeout_is_reported(acs):
+    """A missing arrival at the grid barrier (injected on the host side, no GPU fault)
+    ends the launch after the bounded wait and is reported as ACS_E_TIMEOUT."""
+    inst = _instances(8, 4, 64, 200)
+    b = acs.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+                  [i.bc for i in inst], "f32")
+    b.set_states([i.phi0().astype(np.float32) for i in inst])
+    L = acs.lib()
+    assert L.acs_batch_inject_fault(b.b, 1) == 0
+    b.step(4)
+    with pytest.raises(acs.AcsError) as e:
+        b.observe()
+    assert e.value.status == -4
+    assert L.acs_batch_inject_fault(b.b, 0) == 0
+    b.set_states([i.phi0().astype(np.float32) for i in inst])
+    b.step(4)
+    E, M = b.observe()
+    assert np.isfinite(E).all() and (M <= 1.0).all()
