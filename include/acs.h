@@ -146,6 +146,30 @@ ACS_API int acs_set_kernel(acs_ctx* ctx, int kernel, int depth);
 /* The variant acs_step() uses (after autotuning, for ACS_KERNEL_AUTO). */
 ACS_API int acs_get_kernel(const acs_ctx* ctx, int* kernel, int* depth);
 
+/* Number of tile shapes (rows per thread x ring depth) the tiled kernels offer. */
+ACS_API int acs_num_variants(void);
+
+/*
+ * acs_set_variant -- tile shape of the tiled kernels (0 .. acs_num_variants() - 1) and
+ * the work of one CTA: z planes (3D) or 16-row blocks (2D) per CTA, 0 = chosen from
+ * the occupancy.  Results do not depend on it (bit-identical states).
+ */
+ACS_API int acs_set_variant(acs_ctx* ctx, int variant, int chunk);
+ACS_API int acs_get_variant(const acs_ctx* ctx, int* variant, int* chunk);
+
+/*
+ * acs_autotune -- time every kernel variant available for this problem on the bound
+ * buffers (candidates read the state and write only the work buffer, so the state is
+ * unchanged), keep the fastest, and record it in the tuning cache, a text file named
+ * by $ACS_TUNE_CACHE (default $HOME/.cache/acs_tune.txt; no file if neither is set)
+ * keyed by (device, dims, n, bc, dtype, scheme).  A context created with
+ * ACS_KERNEL_AUTO (the default) runs it on its first acs_step for problems of at least
+ * 2^20 unknowns, unless the cache already holds the key or $ACS_AUTOTUNE is "0"; call
+ * it explicitly before capturing the stream into a CUDA graph.  Synchronizes.
+ * *us_per_step (may be NULL) receives the winner's time per step in microseconds.
+ */
+ACS_API int acs_autotune(acs_ctx* ctx, double* us_per_step);
+
 /*
  * acs_step -- advance the state by n_steps >= 0 steps of Eq. (IE-FD), in place:
  * on completion (stream order) d_phi holds phi^{n + n_steps}.  Asynchronous.

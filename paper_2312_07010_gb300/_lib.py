@@ -37,6 +37,10 @@ SIGNATURES = {
     "acs_set_scheme": (_c.c_int, [_vp, _c.c_int]),
     "acs_set_kernel": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
     "acs_get_kernel": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "acs_num_variants": (_c.c_int, []),
+    "acs_set_variant": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
+    "acs_get_variant": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "acs_autotune": (_c.c_int, [_vp, _dp]),
     "acs_step": (_c.c_int, [_vp, _i64]),
     "acs_steps_done": (_i64, [_vp]),
     "acs_energy": (_c.c_int, [_vp, _dp]),

@@ -3,12 +3,14 @@
 // reductions and state transfer for single problems.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "acs_host.h"
+#include "stream_tile.cuh"
 
 namespace acs {
 
@@ -101,6 +103,13 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
     const double ulp1 = sizeof(T) == 4 ? std::ldexp(1.0, -23) : std::ldexp(1.0, -52);
     c.clamp_hi = (T)(1.0 + 16.0 * ulp1);
     c.clamp = mp_ok ? 1 : 0;
+    // fast path of the tiled kernels: the series range, and with the rounding guard
+    // on, |xi| <= 1 + 8 ulp (exact root within [-1, 1] up to rounding)
+    if (c.solve == kSolveSeries) {
+        double f2 = (double)c.xi2max;
+        if (c.clamp) f2 = std::min(f2, (1.0 + 8.0 * ulp1) * (1.0 + 8.0 * ulp1));
+        c.fast2max = (T)f2;
+    }
     return c;
 }
 template Coef<float> make_coef<float>(int, double, double, int, bool);
@@ -154,7 +163,9 @@ struct acs_ctx {
     double* result;
     double* log;
     int* err;          // set by kernels whose bounded waits gave up
-    int zchunk;        // z planes per CTA of the 3D tiled kernel (0: default)
+    int zchunk;        // z planes (3D) / row blocks (2D) per CTA of the tiled kernels (0: default)
+    int variant;       // tile shape of the tiled kernels
+    bool tuned;        // the autotuner has run (or the cache answered) for this context
     int64_t steps_done;
     std::vector<GraphEntry> graphs;
     // adjoint recording
@@ -196,7 +207,7 @@ static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaS
         if (c->kernel == ACS_KERNEL_TEMPORAL)
             return launch_step_temporal<float>(c->dims, c->bc, k, s, d, c->g, c->cf, c->err, st);
         if (c->kernel == ACS_KERNEL_TILED)
-            return launch_step_tiled<float>(c->dims, c->bc, s, d, c->g, c->cf, c->zchunk, c->err, st);
+            return launch_step_tiled<float>(c->dims, c->bc, s, d, c->g, c->cf, c->variant, c->zchunk, c->err, st);
         return launch_step_naive<float>(c->dims, c->bc, s, d, c->g, c->cf, st);
     }
     const double* s = (const double*)src;
@@ -204,7 +215,7 @@ static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaS
     if (c->kernel == ACS_KERNEL_TEMPORAL)
         return launch_step_temporal<double>(c->dims, c->bc, k, s, d, c->g, c->cd, c->err, st);
     if (c->kernel == ACS_KERNEL_TILED)
-        return launch_step_tiled<double>(c->dims, c->bc, s, d, c->g, c->cd, c->zchunk, c->err, st);
+        return launch_step_tiled<double>(c->dims, c->bc, s, d, c->g, c->cd, c->variant, c->zchunk, c->err, st);
     return launch_step_naive<double>(c->dims, c->bc, s, d, c->g, c->cd, st);
 }
 
@@ -241,8 +252,11 @@ static cudaError_t enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st) {
     return cudaSuccess;
 }
 
+static int maybe_autotune(acs_ctx* c);
+
 static int run_steps(acs_ctx* c, int64_t n) {
     if (n <= 0) return ACS_OK;
+    if (int rc = maybe_autotune(c)) return rc;
     if (c->grad.active) {
         int rc = grad_record_steps(c, n);
         if (rc) return rc;
@@ -305,7 +319,9 @@ static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, c
 namespace acs {
 cudaError_t ctx_enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st) { return enqueue_steps(c, n, st); }
 cudaError_t ctx_launch_one(acs_ctx* c, const void* src, void* dst, cudaStream_t st) {
-    // one plain step with the naive kernel's arithmetic (identical bits to every variant)
+    // one step; every variant gives identical bits, so use the context's tiled kernel
+    // when it has one
+    if (c->kernel == ACS_KERNEL_TILED) return launch_k(c, 1, src, dst, st);
     if (c->dtype == ACS_F32)
         return launch_step_naive<float>(c->dims, c->bc, (const float*)src, (float*)dst, c->g, c->cf, st);
     return launch_step_naive<double>(c->dims, c->bc, (const double*)src, (double*)dst, c->g, c->cd, st);
@@ -389,6 +405,8 @@ ACS_API int acs_create(int dims, const int64_t n[3], double eps, double dt, doub
     c->steps_done = 0;
     c->err = nullptr;
     c->zchunk = 0;
+    c->variant = 0;
+    c->tuned = false;
     c->grad = GradState();
     resolve_auto_kernel(c->dims, c->dtype, c->bc, c->g, &c->kernel, &c->depth);
     *out = c;
@@ -570,6 +588,84 @@ ACS_API int acs_run_logged(acs_ctx* c, int64_t n_steps, int64_t every, double* h
     return finite ? ACS_OK : ACS_E_NONFINITE;
 }
 
+ACS_API int acs_num_variants(void) { return kNumTileVariants; }
+
+ACS_API int acs_set_variant(acs_ctx* c, int variant, int chunk) {
+    if (!c || variant < 0 || variant >= kNumTileVariants || chunk < 0) return ACS_E_INVAL;
+    c->variant = variant;
+    c->zchunk = chunk;
+    drop_graphs(c);
+    return ACS_OK;
+}
+
+ACS_API int acs_get_variant(const acs_ctx* c, int* variant, int* chunk) {
+    if (!c) return ACS_E_INVAL;
+    if (variant) *variant = c->variant;
+    if (chunk) *chunk = c->zchunk;
+    return ACS_OK;
+}
+
+ACS_API int acs_autotune(acs_ctx* c, double* us_per_step) {
+    if (!c) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    if (c->grad.active) return ACS_E_STATE;
+    struct Cand { int kernel, depth, variant, chunk; };
+    std::vector<Cand> cands;
+    cands.push_back({ACS_KERNEL_NAIVE, 1, 0, 0});
+    if (tiled_supported(c->dims, c->dtype, c->g)) {
+        for (int v = 0; v < kNumTileVariants; ++v) {
+            cands.push_back({ACS_KERNEL_TILED, 1, v, 0});
+            if (c->dims == 3 && c->g.nz >= 64) {
+                cands.push_back({ACS_KERNEL_TILED, 1, v, 16});
+                cands.push_back({ACS_KERNEL_TILED, 1, v, 32});
+            }
+        }
+    }
+    for (int k = 2; k <= 8; ++k)
+        if (temporal_supported(c->dims, c->dtype, k, c->g)) cands.push_back({ACS_KERNEL_TEMPORAL, k, 0, 0});
+    const Cand saved = {c->kernel, c->depth, c->variant, c->zchunk};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ACS_E_CUDA;
+    double best = 1e300;
+    Cand win = saved;
+    const double per_launch_units = (double)c->g.total;
+    for (const Cand& k : cands) {
+        c->kernel = k.kernel;
+        c->depth = k.depth;
+        c->variant = k.variant;
+        c->zchunk = k.chunk;
+        const int steps = k.kernel == ACS_KERNEL_TEMPORAL ? k.depth : 1;
+        // warm up, then time launches phi -> work (the state is only read)
+        if (launch_k(c, steps, c->phi, c->other, c->stream) != cudaSuccess) { cudaGetLastError(); continue; }
+        int reps = 3;
+        for (int round = 0; round < 2; ++round) {
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < reps; ++r) launch_k(c, steps, c->phi, c->other, c->stream);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return ACS_E_CUDA; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double us = 1e3 * ms / reps / steps;
+            if (round == 1 && us < best) { best = us; win = k; }
+            // second round: enough launches for about 2 ms
+            reps = (int)std::min<double>(200.0, std::max(3.0, 2000.0 / std::max(1e-3, 1e3 * ms / reps)));
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)per_launch_units;
+    c->kernel = win.kernel;
+    c->depth = win.depth;
+    c->variant = win.variant;
+    c->zchunk = win.chunk;
+    c->tuned = true;
+    drop_graphs(c);
+    if (int rc = check_err_flag(c)) return rc;
+    tune_cache_store(c->dims, c->n, c->bc, c->dtype, c->scheme, win.kernel, win.depth, win.variant, win.chunk, best);
+    if (us_per_step) *us_per_step = best;
+    return ACS_OK;
+}
+
 ACS_API int acs_sync(acs_ctx* c) {
     if (!c) return ACS_E_INVAL;
     if (!c->bound) return ACS_OK;
@@ -586,3 +682,23 @@ ACS_API void acs_destroy(acs_ctx* c) {
 }
 
 }  // extern "C"
+
+// ACS_KERNEL_AUTO: on the first step of a large enough problem, take the cached
+// choice for this problem or run the autotuner.
+static int maybe_autotune(acs_ctx* c) {
+    if (c->tuned || c->kernel_req != ACS_KERNEL_AUTO || c->grad.active) return ACS_OK;
+    c->tuned = true;
+    const char* env = std::getenv("ACS_AUTOTUNE");
+    int k, d, v, ch;
+    if (tune_cache_lookup(c->dims, c->n, c->bc, c->dtype, c->scheme, &k, &d, &v, &ch)) {
+        const bool ok = (k == ACS_KERNEL_NAIVE) || (k == ACS_KERNEL_TILED && tiled_supported(c->dims, c->dtype, c->g)) ||
+                        (k == ACS_KERNEL_TEMPORAL && temporal_supported(c->dims, c->dtype, d, c->g));
+        if (ok && v >= 0 && v < kNumTileVariants) {
+            c->kernel = k; c->depth = d; c->variant = v; c->zchunk = ch;
+            drop_graphs(c);
+            return ACS_OK;
+        }
+    }
+    if (c->g.total < (int64_t(1) << 20) || (env && std::strcmp(env, "0") == 0)) return ACS_OK;
+    return acs_autotune(c, nullptr);
+}

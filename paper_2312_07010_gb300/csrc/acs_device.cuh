@@ -39,6 +39,7 @@ struct Coef {
     T lam, c0, a, b, three_a;
     T q[10];      // kSolveSeries: theta = xi * sum_k q[k] xi^(2k)
     T xi2max;     // kSolveSeries applies while xi^2 <= xi2max
+    T fast2max;   // several-points fast path (tiled kernels): xi^2 bound, see roots()
     T rb, t;      // kSolveNewton: 1/b, a/b
     T ymax;       // kSolveNewton applies while y = t (xi/b)^2 <= ymax
     int newton;   // kSolveNewton: corrections after the seed (1..3)
@@ -137,21 +138,6 @@ __device__ __forceinline__ T predictor(T p, T s, const Coef<T>& c) {
     const T p2 = p * p;
     return dfma(c.lam, s, p * dfma(-c.a, p2, c.c0));
 }
-template <typename T>
-__device__ __forceinline__ T series_root(T xi, const Coef<T>& c) {
-    constexpr int NT = SeriesTerms<T>::value;
-    const T x2 = xi * xi;
-    T P = c.q[NT - 1];
-#pragma unroll
-    for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2, c.q[k]);
-    T th = xi * P;
-    if (c.clamp) {
-        const T ath = th < T(0) ? -th : th;
-        if (ath > T(1) && ath <= c.clamp_hi) th = th < T(0) ? T(-1) : T(1);
-    }
-    return th;
-}
-
 // The new value of one unknown from its old value p and the sum s of its 2d
 // ghost-ruled neighbours.
 template <typename T, int SOLVE>

@@ -49,6 +49,12 @@ cudaError_t ctx_enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st);
 cudaError_t ctx_launch_one(acs_ctx* c, const void* src, void* dst, cudaStream_t st);
 CtxView ctx_view(acs_ctx* c);
 
+// Tuning cache (tune_cache.cu): a text file of the autotuner's choices.
+bool tune_cache_lookup(int dims, const int64_t* n, int bc, int dtype, int scheme, int* kernel, int* depth,
+                       int* variant, int* chunk);
+void tune_cache_store(int dims, const int64_t* n, int bc, int dtype, int scheme, int kernel, int depth, int variant,
+                      int chunk, double us);
+
 // Implemented in adjoint.cu.
 int grad_on_set_state(acs_ctx* c);
 int grad_record_steps(acs_ctx* c, int64_t n);

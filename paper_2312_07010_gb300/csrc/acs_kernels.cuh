@@ -20,9 +20,11 @@ cudaError_t launch_step_naive(int dims, int bc, const T* src, T* dst, const Geo&
 
 // Tiled variants: return cudaErrorNotSupported when the shape is not covered.
 // err: device int set to 1 when a bounded wait inside the kernel gives up.
+// variant: tile shape index (0 .. kNumTileVariants - 1); chunk: z planes (3D) or
+// 16-row blocks (2D) per CTA, 0 = chosen from the occupancy.
 template <typename T>
-cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk,
-                              int* err, cudaStream_t st);
+cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant,
+                              int chunk, int* err, cudaStream_t st);
 template <typename T>
 cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* dst, const Geo& g,
                                  const Coef<T>& c, int* err, cudaStream_t st);

@@ -20,6 +20,7 @@
 
 #include "acs_host.h"
 #include "acs_reduce.cuh"
+#include "tile2d.cuh"
 
 namespace acs {
 
@@ -104,10 +105,14 @@ __global__ void __launch_bounds__(256) k_adjoint(const T* __restrict__ phin, con
     if (threadIdx.x == 0) part[blockIdx.x] = ge;
 }
 
-// acc += sum of the step's partials, in a fixed order.
-__global__ void k_adjoint_finish(const CSum* part, int nparts, CSum* acc) {
+// acc += the partials of a segment: steps x nparts entries, in a fixed order.
+__global__ void k_adjoint_finish(const CSum* part, int steps, int stride, int nparts, CSum* acc) {
     CSum s{0.0, 0.0};
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s = cmerge(s, part[i]);
+    const int total = steps * nparts;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int st = i / nparts, b = i - st * nparts;
+        s = cmerge(s, part[(size_t)st * stride + b]);
+    }
     __shared__ CSum scratch[32];
     s = block_csum(s, scratch);
     if (threadIdx.x == 0) acc[0] = cmerge(acc[0], s);
@@ -115,9 +120,84 @@ __global__ void k_adjoint_finish(const CSum* part, int nparts, CSum* acc) {
 
 __global__ void k_zero_acc(CSum* acc) { acc[0] = CSum{0.0, 0.0}; }
 
+// 2D adjoint step from shared-memory tiles: phi^n, phi^{n+1} and adj^{n+1} are staged
+// with the ghost rule (cp.async), mu = adj^{n+1} / (3 a (phi^{n+1})^2 + b) is formed
+// once per staged point in place, then each thread updates its 8 points.  The ghost of
+// mu follows the same rule as phi (the stencil is symmetric).
+template <typename T, int BC>
+__global__ void __launch_bounds__(256) k_adjoint2d(const T* __restrict__ phin, const T* __restrict__ phin1,
+                                                   const T* __restrict__ adj1, T* __restrict__ adj0, Geo g,
+                                                   Coef<T> cf, int ntx, int nty, int per_cta, CSum* part) {
+    using TT = Tile2<T>;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* P = reinterpret_cast<T*>(sm_raw);
+    T* Q = P + TT::N;
+    T* M = Q + TT::N;
+    const int ny = (int)g.ny, nx = (int)g.nx;
+    const int ntiles = ntx * nty;
+    const int t0 = blockIdx.x * per_cta, t1 = min(t0 + per_cta, ntiles);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    CSum ge{0.0, 0.0};
+    for (int t = t0; t < t1; ++t) {
+        const int x0 = (t / nty) * TT::TX, y0 = (t % nty) * TT::TY;
+        stage_tile<T>(P, phin, ny, nx, BC, x0, y0);
+        stage_tile<T>(Q, phin1, ny, nx, BC, x0, y0);
+        stage_tile<T>(M, adj1, ny, nx, BC, x0, y0);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        for (int i = threadIdx.x; i < TT::N; i += TT::THREADS) {
+            const T q = Q[i];
+            M[i] = M[i] / dfma(cf.three_a, q * q, cf.b);
+        }
+        __syncthreads();
+        T tile_sum = T(0);
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int r = 2 * w + rr;
+            const int gy = y0 + r;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int cx = lane + 32 * k;
+                const int gx = x0 + cx;
+                const int i = (r + 1) * TT::BW + (cx + 1);
+                const T mu = M[i], p = P[i];
+                const T smu = nsum(M[i - TT::BW], M[i + TT::BW], M[i - 1], M[i + 1]);
+                const T sphi = nsum(P[i - TT::BW], P[i + TT::BW], P[i - 1], P[i + 1]);
+                if (gy < ny && gx < nx) {
+                    adj0[(int64_t)gy * nx + gx] = dfma(cf.lam, smu, mu * dfma(-cf.three_a, p * p, cf.c0));
+                    tile_sum = dfma(mu, sphi - T(4) * p, tile_sum);
+                }
+            }
+        }
+        cadd(ge, (double)tile_sum);
+        __syncthreads();
+    }
+    __shared__ CSum scratch[32];
+    ge = block_csum(ge, scratch);
+    if (threadIdx.x == 0) part[blockIdx.x] = ge;
+}
+
+// One adjoint step writing its per-block eps^2 partials to `part` (kMaxRedBlocks
+// entries); returns the number of partials used in *nparts.
 template <typename T>
 static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin1, const T* adj1, T* adj0,
-                                  const Geo& g, const Coef<T>& cf, CSum* part, CSum* acc, cudaStream_t st) {
+                                  const Geo& g, const Coef<T>& cf, CSum* part, int* nparts, cudaStream_t st) {
+    if (dims == 2 && g.nx < (1 << 30) && g.ny < (1 << 30)) {
+        using TT = Tile2<T>;
+        const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX), nty = (int)((g.ny + TT::TY - 1) / TT::TY);
+        const int64_t ntiles = (int64_t)ntx * nty;
+        const int per = (int)std::max<int64_t>(1, (ntiles + kMaxRedBlocks - 1) / kMaxRedBlocks);
+        const int grid = (int)((ntiles + per - 1) / per);
+        const size_t smem = 3 * TT::N * sizeof(T);
+        cudaError_t e = cudaSuccess;
+        auto kern = bc == 0 ? k_adjoint2d<T, 0> : (bc == 1 ? k_adjoint2d<T, 1> : k_adjoint2d<T, 2>);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, TT::THREADS, smem, st>>>(phin, phin1, adj1, adj0, g, cf, ntx, nty, per, part);
+        *nparts = grid;
+        return cudaGetLastError();
+    }
     const int nb = reduce_blocks(g);
 #define ACS_ADJ_CASE(D, B) \
     if (dims == D && bc == B) k_adjoint<T, D, B><<<nb, 256, 0, st>>>(phin, phin1, adj1, adj0, g, cf, part); else
@@ -126,9 +206,7 @@ static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin
     ACS_ADJ_CASE(3, 0) ACS_ADJ_CASE(3, 1) ACS_ADJ_CASE(3, 2)
     return cudaErrorInvalidValue;
 #undef ACS_ADJ_CASE
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_adjoint_finish<<<1, 256, 0, st>>>(part, nb, acc);
+    *nparts = nb;
     return cudaGetLastError();
 }
 
@@ -153,7 +231,7 @@ GradLayout layout(const CtxView& v, int64_t max_steps, int64_t every) {
     L.adjA = L.seg + L.sb * (size_t)every;
     L.adjB = L.adjA + L.sb;
     L.part = L.adjB + L.sb;
-    L.acc = L.part + al(sizeof(CSum) * kMaxRedBlocks);
+    L.acc = L.part + al(sizeof(CSum) * kMaxRedBlocks * (size_t)every);
     L.total = L.acc + kA;
     return L;
 }
@@ -252,19 +330,24 @@ ACS_API int acs_grad(acs_ctx* c, const void* d_dL_dphiT, void* d_dL_dphi0, doubl
                 if (ctx_launch_one(c, prev, dst, st) != cudaSuccess) return ACS_E_CUDA;
                 prev = dst;
             }
+            int nparts = 0;
             for (int64_t k = m - 1; k >= 0; --k) {
                 const char* pk = k == 0 ? ck : G.buf + L.seg + L.sb * (size_t)(k - 1);
                 const char* pk1 = G.buf + L.seg + L.sb * (size_t)k;
+                CSum* pst = part + (size_t)(m - 1 - k) * kMaxRedBlocks;
                 cudaError_t e;
                 if (v.dtype == ACS_F32)
                     e = launch_adjoint<float>(v.dims, v.bc, (const float*)pk, (const float*)pk1, (const float*)A,
-                                              (float*)B, v.g, v.cf, part, acc, st);
+                                              (float*)B, v.g, v.cf, pst, &nparts, st);
                 else
                     e = launch_adjoint<double>(v.dims, v.bc, (const double*)pk, (const double*)pk1,
-                                               (const double*)A, (double*)B, v.g, v.cd, part, acc, st);
+                                               (const double*)A, (double*)B, v.g, v.cd, pst, &nparts, st);
                 if (e != cudaSuccess) return ACS_E_CUDA;
                 std::swap(A, B);
             }
+            // the segment's eps^2 partials, in a fixed order
+            k_adjoint_finish<<<1, 256, 0, st>>>(part, (int)m, kMaxRedBlocks, nparts, acc);
+            if (cudaGetLastError() != cudaSuccess) return ACS_E_CUDA;
         }
     }
     if (cudaMemcpyAsync(d_dL_dphi0, A, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return ACS_E_CUDA;

@@ -14,13 +14,14 @@
 
 namespace acs {
 
-template <typename T, int BC, int SOLVE>
+template <typename T, int BC, int SOLVE, int RPT, int SS>
 __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUtensorMap tmap,
                                                     const T* __restrict__ src, T* __restrict__ dst, Geo g,
                                                     Coef<T> c, int ybchunk, int* err) {
-    using TT = Tile3<T>;
+    using TT = Tile3<T, RPT, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
+    constexpr int NP = RPT * VX;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     uint64_t* full = reinterpret_cast<uint64_t*>(base);
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
     const int tid = ly * 32 + lx;
     const int xl = lx * VX;
     const int gx = x0 + xl;
-    const int r0 = 2 * ly;
+    const int r0 = RPT * ly;
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
@@ -59,7 +60,6 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
         for (int b = b0; b <= last_issued; ++b) issue(b);
 
     const int64_t sy = g.sy;
-    const bool edge = BC != ACS_BC_DIRICHLET;  // Neumann / periodic fix-ups at the faces
     const bool xlo = gx == 0, xhi = gx + VX == nx;
     const bool vecok = gx + VX <= nx;
     bool failed = false;
@@ -68,21 +68,21 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
         const bool ok = mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
         const T* cur = ring + (size_t)(k % S) * SLOT_ELEMS;
         const int gy0 = b * TY + r0;
-        T cz[2][VX], xi[2][VX];
-        Vec<T>::get(cur + (r0 + 1) * BW + VX + xl, cz[0]);
-        Vec<T>::get(cur + (r0 + 2) * BW + VX + xl, cz[1]);
+        T cz[RPT][VX], below[VX], above[VX], xi[NP];
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
+        for (int rr = 0; rr < RPT; ++rr) Vec<T>::get(cur + (r0 + rr + 1) * BW + VX + xl, cz[rr]);
+        Vec<T>::get(cur + r0 * BW + VX + xl, below);
+        Vec<T>::get(cur + (r0 + RPT + 1) * BW + VX + xl, above);
+        const bool edge = BC != ACS_BC_DIRICHLET &&
+                          (x0 == 0 || x0 + TX >= nx || b * TY == 0 || (b + 1) * TY >= ny);
+#pragma unroll
+        for (int rr = 0; rr < RPT; ++rr) {
             const int gyr = gy0 + rr;
             T ym[VX], yp[VX];
-            if (rr == 0) {
-                Vec<T>::get(cur + r0 * BW + VX + xl, ym);
 #pragma unroll
-                for (int v = 0; v < VX; ++v) yp[v] = cz[1][v];
-            } else {
-#pragma unroll
-                for (int v = 0; v < VX; ++v) ym[v] = cz[0][v];
-                Vec<T>::get(cur + (r0 + 3) * BW + VX + xl, yp);
+            for (int v = 0; v < VX; ++v) {
+                ym[v] = rr == 0 ? below[v] : cz[rr - 1][v];
+                yp[v] = rr == RPT - 1 ? above[v] : cz[rr + 1][v];
             }
             T left = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
             T right = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
@@ -112,43 +112,21 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
             for (int v = 0; v < VX; ++v) {
                 const T xm = v == 0 ? left : cz[rr][v - 1];
                 const T xp = v == VX - 1 ? right : cz[rr][v + 1];
-                xi[rr][v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
+                xi[rr * VX + v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
             }
         }
-        T out[2][VX];
-        bool fast = SOLVE == kSolveSeries;
-        if (SOLVE == kSolveSeries) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) fast = fast && (xi[rr][v] * xi[rr][v] <= c.xi2max);
-        }
-        if (fast) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) out[rr][v] = series_root(xi[rr][v], c);
-        } else if (SOLVE == kSolveFex) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) out[rr][v] = xi[rr][v];
-        } else {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) out[rr][v] = cubic_root<T, SOLVE>(xi[rr][v], c);
-        }
+        T out[NP];
+        roots<T, SOLVE, NP>(xi, out, c);
         T* o = dst + (int64_t)gy0 * sy + gx;
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
+        for (int rr = 0; rr < RPT; ++rr) {
             if (gy0 + rr >= ny) continue;
             if (vecok) {
-                Vec<T>::put(o + rr * sy, out[rr]);
+                Vec<T>::put(o + rr * sy, &out[rr * VX]);
             } else {
 #pragma unroll
                 for (int v = 0; v < VX; ++v)
-                    if (gx + v < nx) o[rr * sy + v] = out[rr][v];
+                    if (gx + v < nx) o[rr * sy + v] = out[rr * VX + v];
             }
         }
         failed = __syncthreads_or(!ok);
@@ -174,10 +152,10 @@ bool step2d_tma_supported(int dtype, const Geo& g) {
     return g.nz == 1 && (g.nx * esize) % 16 == 0 && g.nx < (1 << 30) && g.ny < (1 << 30);
 }
 
-template <typename T>
-cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ybchunk, int* err,
-                              cudaStream_t st) {
-    using TT = Tile3<T>;
+template <typename T, int RPT, int SS>
+static cudaError_t launch2d_variant(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ybchunk,
+                                    int* err, cudaStream_t st) {
+    using TT = Tile3<T, RPT, SS>;
     CUtensorMap map;
     const uint64_t dims[2] = {(uint64_t)g.nx, (uint64_t)g.ny};
     const uint32_t box[2] = {(uint32_t)TT::BW, (uint32_t)TT::BH};
@@ -192,25 +170,31 @@ cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const 
     }
     const int nchunks = (nyb + ybchunk - 1) / ybchunk;
     if (nchunks > 65535) return cudaErrorNotSupported;
-    dim3 grid((unsigned)ntx, (unsigned)nchunks), block(32, 8);
     cudaError_t e = cudaSuccess;
-#define ACS_2DT_CASE(B)                                                                                  \
-    if (bc == B) {                                                                                       \
-        ACS_SOLVE_DISPATCH(c.solve, SV, {                                                                \
-            auto kern = k_step2d_tma<T, B, SV>;                                                          \
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);  \
-            if (e == cudaSuccess) kern<<<grid, block, TT::SMEM, st>>>(map, src, dst, g, c, ybchunk, err); \
-        });                                                                                              \
-    }
-    ACS_2DT_CASE(0) ACS_2DT_CASE(1) ACS_2DT_CASE(2)
-#undef ACS_2DT_CASE
+    ACS_SOLVE_DISPATCH(c.solve, SV, {
+        auto kern = bc == 0 ? k_step2d_tma<T, 0, SV, RPT, SS>
+                            : (bc == 1 ? k_step2d_tma<T, 1, SV, RPT, SS> : k_step2d_tma<T, 2, SV, RPT, SS>);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);
+        if (e == cudaSuccess)
+            kern<<<dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), TT::SMEM, st>>>(map, src, dst, g, c, ybchunk,
+                                                                                        err);
+    });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step2d_tma<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int*,
-                                              cudaStream_t);
+template <typename T>
+cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant,
+                              int ybchunk, int* err, cudaStream_t st) {
+    cudaError_t e = cudaErrorInvalidValue;
+    ACS_TILE_VARIANT_DISPATCH(variant, RPTV, SV,
+                              (e = launch2d_variant<T, RPTV, SV>(bc, src, dst, g, c, ybchunk, err, st)));
+    return e;
+}
+
+template cudaError_t launch_step2d_tma<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int,
+                                              int*, cudaStream_t);
 template cudaError_t launch_step2d_tma<double>(int, const double*, double*, const Geo&, const Coef<double>&, int,
-                                               int*, cudaStream_t);
+                                               int, int*, cudaStream_t);
 
 }  // namespace acs

@@ -20,13 +20,14 @@
 
 namespace acs {
 
-template <typename T, int BC, int SOLVE>
+template <typename T, int BC, int SOLVE, int RPT, int SS>
 __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src,
                                                 T* __restrict__ dst, Geo g, Coef<T> c, int ntx, int zchunk,
                                                 int* err) {
-    using TT = Tile3<T>;
+    using TT = Tile3<T, RPT, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
+    constexpr int NP = RPT * VX;  // points per thread per plane
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // align the ring to 128 bytes whatever the base alignment of dynamic shared memory
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -42,8 +43,8 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
     const int tid = ly * 32 + lx;
     const int xl = lx * VX;
     const int gx = x0 + xl;
-    const int r0 = 2 * ly;
-    const int gy[2] = {y0 + r0, y0 + r0 + 1};
+    const int r0 = RPT * ly;      // first tile row of this thread
+    const int gy0 = y0 + r0;      // its grid row
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
@@ -51,10 +52,10 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
     }
     __syncthreads();
 
+    auto slot_of = [&](int p) { return ring + (size_t)((p - (z0 - 1)) % S) * SLOT_ELEMS; };
     auto issue = [&](int p) {
         const int k = p - (z0 - 1);
-        const int s = k % S;
-        T* dstp = ring + (size_t)s * SLOT_ELEMS;
+        T* dstp = slot_of(p);
         // self-check of the TMA preconditions: a misaligned destination or x offset is
         // recorded and the copy skipped (the consumers' bounded wait then reports it)
         if ((smem_u32(dstp) & 127u) != 0u || (((x0 - VX) * (int)sizeof(T)) & 15) != 0) {
@@ -62,34 +63,31 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
             return;
         }
         fence_proxy_async();
-        mbar_arrive_expect_tx(&full[s], TT::SLOT_BYTES);
-        tma_load_3d(dstp, &tmap, &full[s], x0 - VX, y0 - 1, zsrc<BC>(p, nz));
+        mbar_arrive_expect_tx(&full[k % S], TT::SLOT_BYTES);
+        tma_load_3d(dstp, &tmap, &full[k % S], x0 - VX, y0 - 1, zsrc<BC>(p, nz));
     };
-    auto slot_of = [&](int p) { return ring + (size_t)((p - (z0 - 1)) % S) * SLOT_ELEMS; };
     auto wait_plane = [&](int p) -> bool {
         const int k = p - (z0 - 1);
         return mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
     };
-    // my two rows x VX values of a plane, from shared memory
-    auto read_mine = [&](const T* sl, T (&o)[2][VX]) {
-        Vec<T>::get(sl + (r0 + 1) * BW + VX + xl, o[0]);
-        Vec<T>::get(sl + (r0 + 2) * BW + VX + xl, o[1]);
+    // this thread's RPT rows x VX values of a plane
+    auto read_mine = [&](const T* sl, T (&o)[RPT][VX]) {
+#pragma unroll
+        for (int rr = 0; rr < RPT; ++rr) Vec<T>::get(sl + (r0 + rr + 1) * BW + VX + xl, o[rr]);
     };
 
-    int last_issued = z0 - 2;
-    if (tid == 0) {
-        for (int p = z0 - 1; p <= min(z0 + S - 2, z1); ++p) issue(p);
-    }
-    last_issued = min(z0 + S - 2, z1);
+    int last_issued = min(z0 + S - 2, z1);
+    if (tid == 0)
+        for (int p = z0 - 1; p <= last_issued; ++p) issue(p);
 
-    T zm[2][VX], cz[2][VX];
+    T zm[RPT][VX], cz[RPT][VX];
     bool ok = wait_plane(z0 - 1);
     read_mine(slot_of(z0 - 1), zm);
     ok = wait_plane(z0) && ok;
     read_mine(slot_of(z0), cz);
     bool failed = __syncthreads_or(!ok);
     if (!failed && tid == 0 && z0 + S - 1 <= z1) issue(z0 + S - 1);
-    last_issued = failed ? last_issued : min(z0 + S - 1, z1);
+    if (!failed) last_issued = min(z0 + S - 1, z1);
 
     const int64_t sy = g.sy, sz = g.sz;
     // Boundary handling hoisted out of the z loop.  Only a CTA whose tile touches an
@@ -97,36 +95,33 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
     // (TMA zero fill), and z faces are handled by the producer's plane choice.
     const bool edge = BC != ACS_BC_DIRICHLET && (x0 == 0 || x0 + TX >= nx || y0 == 0 || y0 + TY >= ny);
     const bool xlo = gx == 0, xhi = gx + VX == nx;
-    const bool rowok0 = gy[0] < ny, rowok1 = gy[1] < ny;
     const bool vecok = gx + VX <= nx;
-    T* o = dst + (int64_t)z0 * sz + (int64_t)gy[0] * sy + gx;
+    T* o = dst + (int64_t)z0 * sz + (int64_t)gy0 * sy + gx;
 
     // One plane: zm / cz / zp are this thread's values at z-1, z, z+1.
-    auto plane = [&](int z, T (&zm)[2][VX], T (&cz)[2][VX], T (&zp)[2][VX]) {
+    auto plane = [&](int z, T (&zm)[RPT][VX], T (&cz)[RPT][VX], T (&zp)[RPT][VX]) {
         ok = wait_plane(z + 1);
         read_mine(slot_of(z + 1), zp);
         const T* cur = slot_of(z);
-        T xi[2][VX];
+        T xi[NP];
+        T below[VX], above[VX];  // rows r0 - 1 and r0 + RPT
+        Vec<T>::get(cur + r0 * BW + VX + xl, below);
+        Vec<T>::get(cur + (r0 + RPT + 1) * BW + VX + xl, above);
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int r = r0 + rr;
+        for (int rr = 0; rr < RPT; ++rr) {
+            const int gyr = gy0 + rr;
             T ym[VX], yp[VX];
-            if (rr == 0) {
-                Vec<T>::get(cur + r * BW + VX + xl, ym);  // row r - 1 (box row r)
 #pragma unroll
-                for (int v = 0; v < VX; ++v) yp[v] = cz[1][v];
-            } else {
-#pragma unroll
-                for (int v = 0; v < VX; ++v) ym[v] = cz[0][v];
-                Vec<T>::get(cur + (r + 2) * BW + VX + xl, yp);  // row r + 1 (box row r + 2)
+            for (int v = 0; v < VX; ++v) {
+                ym[v] = rr == 0 ? below[v] : cz[rr - 1][v];
+                yp[v] = rr == RPT - 1 ? above[v] : cz[rr + 1][v];
             }
             // x neighbours across lanes; the tile's outer two come from the halo group
             T left = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
             T right = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
-            if (lx == 0) left = cur[(r + 1) * BW + VX - 1];
-            if (lx == 31) right = cur[(r + 1) * BW + VX + TX];
-            if (edge && (rr == 0 ? rowok0 : rowok1)) {
-                const int gyr = gy[rr];
+            if (lx == 0) left = cur[(r0 + rr + 1) * BW + VX - 1];
+            if (lx == 31) right = cur[(r0 + rr + 1) * BW + VX + TX];
+            if (edge && gyr < ny) {
                 const int64_t rowoff = (int64_t)z * sz + (int64_t)gyr * sy;
                 if (gyr == 0) {
                     if (BC == ACS_BC_NEUMANN) {
@@ -152,42 +147,20 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
                 const T xm = v == 0 ? left : cz[rr][v - 1];
                 const T xp = v == VX - 1 ? right : cz[rr][v + 1];
                 const T s = nsum(zm[rr][v], zp[rr][v], ym[v], yp[v], xm, xp);
-                xi[rr][v] = predictor(cz[rr][v], s, c);
+                xi[rr * VX + v] = predictor(cz[rr][v], s, c);
             }
         }
-        // one decision per thread for the cubic path of its 2 x VX points
-        T out[2][VX];
-        bool fast = SOLVE == kSolveSeries;
-        if (SOLVE == kSolveSeries) {
+        T out[NP];
+        roots<T, SOLVE, NP>(xi, out, c);
 #pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
+        for (int rr = 0; rr < RPT; ++rr) {
+            if (gy0 + rr >= ny) continue;
+            if (vecok) {
+                Vec<T>::put(o + rr * sy, &out[rr * VX]);
+            } else {
 #pragma unroll
-                for (int v = 0; v < VX; ++v) fast = fast && (xi[rr][v] * xi[rr][v] <= c.xi2max);
-        }
-        if (fast) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) out[rr][v] = series_root(xi[rr][v], c);
-        } else if (SOLVE == kSolveFex) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) out[rr][v] = xi[rr][v];
-        } else {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) out[rr][v] = cubic_root<T, SOLVE>(xi[rr][v], c);
-        }
-        if (vecok) {
-            if (rowok0) Vec<T>::put(o, out[0]);
-            if (rowok1) Vec<T>::put(o + sy, out[1]);
-        } else {
-#pragma unroll
-            for (int v = 0; v < VX; ++v) {
-                if (gx + v < nx && rowok0) o[v] = out[0][v];
-                if (gx + v < nx && rowok1) o[sy + v] = out[1][v];
+                for (int v = 0; v < VX; ++v)
+                    if (gx + v < nx) o[rr * sy + v] = out[rr * VX + v];
             }
         }
         o += sz;
@@ -197,7 +170,7 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
     };
 
     // the three register sets rotate roles, so the loop is unrolled by three
-    T zq[2][VX];
+    T zq[RPT][VX];
     int z = z0;
     for (; z + 3 <= z1 && !failed; z += 3) {
         plane(z, zm, cz, zq);
@@ -232,11 +205,7 @@ bool step3d_supported(int dtype, const Geo& g) {
 
 // z planes per CTA: minimize (waves of resident CTAs) x (planes per CTA + pipeline
 // fill), the launch's critical path; a chunk also re-reads its two halo planes.
-template <typename T>
-static int choose_zchunk(const Geo& g, int resident) {
-    using TT = Tile3<T>;
-    const int64_t tiles = ((g.nx + TT::TX - 1) / TT::TX) * ((g.ny + TT::TY - 1) / TT::TY);
-    const int64_t nz = g.nz;
+static int choose_zchunk(int64_t tiles, int64_t nz, int resident) {
     int best = (int)nz;
     double best_cost = 1e300;
     for (int64_t zc = std::min<int64_t>(nz, 4); zc <= nz; ++zc) {
@@ -249,48 +218,50 @@ static int choose_zchunk(const Geo& g, int resident) {
     return best;
 }
 
-template <typename T>
-cudaError_t launch_step3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk, int* err,
-                          cudaStream_t st) {
-    using TT = Tile3<T>;
+template <typename T, int RPT, int SS>
+static cudaError_t launch3d_variant(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk,
+                                    int* err, cudaStream_t st) {
+    using TT = Tile3<T, RPT, SS>;
     CUtensorMap map;
     const uint64_t dims[3] = {(uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz};
     const uint32_t box[3] = {(uint32_t)TT::BW, (uint32_t)TT::BH, 1u};
     if (!encode_tensor_map(&map, sizeof(T), 3, src, dims, box)) return cudaErrorNotSupported;
-    if (zchunk <= 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        ACS_SOLVE_DISPATCH(c.solve, SV, {
-            auto kern = bc == 0 ? k_step3d<T, 0, SV> : (bc == 1 ? k_step3d<T, 1, SV> : k_step3d<T, 2, SV>);
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, TT::SMEM);
-        });
-        zchunk = choose_zchunk<T>(g, std::max(1, sms * std::max(1, per_sm)));
-    }
     const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX);
     const int nty = (int)((g.ny + TT::TY - 1) / TT::TY);
-    const int nzc = (int)((g.nz + zchunk - 1) / zchunk);
-    if ((int64_t)ntx * nty > 0x7fffffff || nzc > 65535) return cudaErrorNotSupported;
-    dim3 grid((unsigned)(ntx * nty), (unsigned)nzc), block(32, 8);
+    if ((int64_t)ntx * nty > 0x7fffffff) return cudaErrorNotSupported;
     cudaError_t e = cudaSuccess;
-#define ACS_3D_CASE(B)                                                                                   \
-    if (bc == B) {                                                                                       \
-        ACS_SOLVE_DISPATCH(c.solve, SV, {                                                                \
-            auto kern = k_step3d<T, B, SV>;                                                              \
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);  \
-            if (e == cudaSuccess) kern<<<grid, block, TT::SMEM, st>>>(map, src, dst, g, c, ntx, zchunk, err); \
-        });                                                                                              \
-    }
-    ACS_3D_CASE(0) ACS_3D_CASE(1) ACS_3D_CASE(2)
-#undef ACS_3D_CASE
+    ACS_SOLVE_DISPATCH(c.solve, SV, {
+        auto kern = bc == 0 ? k_step3d<T, 0, SV, RPT, SS>
+                            : (bc == 1 ? k_step3d<T, 1, SV, RPT, SS> : k_step3d<T, 2, SV, RPT, SS>);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);
+        if (e == cudaSuccess && zchunk <= 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, TT::SMEM);
+            zchunk = choose_zchunk((int64_t)ntx * nty, g.nz, std::max(1, sms * std::max(1, per_sm)));
+        }
+        const int nzc = (int)((g.nz + zchunk - 1) / zchunk);
+        if (e == cudaSuccess && nzc > 65535) e = cudaErrorNotSupported;
+        if (e == cudaSuccess)
+            kern<<<dim3((unsigned)(ntx * nty), (unsigned)nzc), dim3(32, 8), TT::SMEM, st>>>(map, src, dst, g, c, ntx,
+                                                                                              zchunk, err);
+    });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step3d<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int*,
+template <typename T>
+cudaError_t launch_step3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant, int zchunk,
+                          int* err, cudaStream_t st) {
+    cudaError_t e = cudaErrorInvalidValue;
+    ACS_TILE_VARIANT_DISPATCH(variant, RPTV, SV, (e = launch3d_variant<T, RPTV, SV>(bc, src, dst, g, c, zchunk, err, st)));
+    return e;
+}
+
+template cudaError_t launch_step3d<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int, int*,
                                           cudaStream_t);
-template cudaError_t launch_step3d<double>(int, const double*, double*, const Geo&, const Coef<double>&, int, int*,
-                                           cudaStream_t);
+template cudaError_t launch_step3d<double>(int, const double*, double*, const Geo&, const Coef<double>&, int, int,
+                                           int*, cudaStream_t);
 
 }  // namespace acs

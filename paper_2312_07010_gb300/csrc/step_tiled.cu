@@ -9,8 +9,8 @@ namespace acs {
 
 bool step3d_supported(int dtype, const Geo& g);
 template <typename T>
-cudaError_t launch_step3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk, int* err,
-                          cudaStream_t st);
+cudaError_t launch_step3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant, int zchunk,
+                          int* err, cudaStream_t st);
 
 bool step2d_supported(const Geo& g);
 template <typename T>
@@ -19,8 +19,8 @@ cudaError_t launch_step2d(int bc, const T* src, T* dst, const Geo& g, const Coef
 
 bool step2d_tma_supported(int dtype, const Geo& g);
 template <typename T>
-cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ybchunk, int* err,
-                              cudaStream_t st);
+cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant,
+                              int ybchunk, int* err, cudaStream_t st);
 
 bool encode_tensor_map(CUtensorMap* map, int esize, int rank, const void* base, const uint64_t* dims,
                        const uint32_t* box) {
@@ -64,13 +64,13 @@ bool temporal_supported(int dims, int dtype, int depth, const Geo& g) {
 }
 
 template <typename T>
-cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk,
-                              int* err, cudaStream_t st) {
-    if (dims == 3) return launch_step3d<T>(bc, src, dst, g, c, zchunk, err, st);
+cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant,
+                              int chunk, int* err, cudaStream_t st) {
+    if (dims == 3) return launch_step3d<T>(bc, src, dst, g, c, variant, chunk, err, st);
     if (dims == 2) {
         if (step2d_tma_supported(sizeof(T) == 4 ? ACS_F32 : ACS_F64, g))
-            return launch_step2d_tma<T>(bc, src, dst, g, c, zchunk, err, st);
-        return launch_step2d<T>(bc, src, dst, g, c, zchunk, st);
+            return launch_step2d_tma<T>(bc, src, dst, g, c, variant, chunk, err, st);
+        return launch_step2d<T>(bc, src, dst, g, c, chunk, st);
     }
     return cudaErrorNotSupported;
 }
@@ -79,9 +79,9 @@ cudaError_t launch_step_temporal(int, int, int, const T*, T*, const Geo&, const 
     return cudaErrorNotSupported;
 }
 template cudaError_t launch_step_tiled<float>(int, int, const float*, float*, const Geo&, const Coef<float>&, int,
-                                              int*, cudaStream_t);
+                                              int, int*, cudaStream_t);
 template cudaError_t launch_step_tiled<double>(int, int, const double*, double*, const Geo&, const Coef<double>&,
-                                               int, int*, cudaStream_t);
+                                               int, int, int*, cudaStream_t);
 template cudaError_t launch_step_temporal<float>(int, int, int, const float*, float*, const Geo&,
                                                  const Coef<float>&, int*, cudaStream_t);
 template cudaError_t launch_step_temporal<double>(int, int, int, const double*, double*, const Geo&,

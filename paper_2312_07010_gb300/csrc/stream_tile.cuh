@@ -6,14 +6,18 @@
 
 namespace acs {
 
-template <typename T>
+// Geometry of a streamed tile: 256 threads = 32 lanes x 8 warps; each thread owns
+// one 16-byte vector (VX values) in RPT consecutive rows, so the tile is
+// TX = 32 VX wide and TY = 8 RPT high; S ring slots of TMA-loaded boxes.
+template <typename T, int RPT_ = 2, int S_ = 4>
 struct Tile3 {
+    static constexpr int RPT = RPT_;                // rows per thread
     static constexpr int VX = 16 / (int)sizeof(T);  // unknowns per 16-byte vector
     static constexpr int TX = 32 * VX;              // tile width
-    static constexpr int TY = 16;                   // tile height: 8 warps x 2 rows
+    static constexpr int TY = 8 * RPT;              // tile height
     static constexpr int BW = TX + 2 * VX;          // box width (16-byte aligned halo)
     static constexpr int BH = TY + 2;               // box height
-    static constexpr int S = 4;                     // ring slots
+    static constexpr int S = S_;                    // ring slots
     static constexpr int SLOT = BW * BH;                        // values in one box
     static constexpr uint32_t SLOT_BYTES = SLOT * sizeof(T);    // bytes one TMA load writes
     // TMA tensor copies need a 128-byte aligned shared-memory destination
@@ -22,7 +26,70 @@ struct Tile3 {
     static constexpr size_t SMEM = 128 + BAR_BYTES + (size_t)S * SLOT_STRIDE;  // + base alignment slack
     static_assert(SLOT_STRIDE % 128 == 0 && S * sizeof(uint64_t) <= BAR_BYTES, "ring layout");
     static_assert((VX * sizeof(T)) % 16 == 0 && (BW * sizeof(T)) % 16 == 0, "16-byte TMA x granularity");
+    static_assert(BW <= 256 && BH <= 256, "TMA box dimensions");
 };
+
+// Tile variants offered to the autotuner: (rows per thread, ring slots).
+constexpr int kNumTileVariants = 3;
+#define ACS_TILE_VARIANT_DISPATCH(var, RPTV, SV, ...)          \
+    do {                                                      \
+        if ((var) == 1) {                                     \
+            constexpr int RPTV = 2, SV = 6;                   \
+            __VA_ARGS__;                                      \
+        } else if ((var) == 2) {                              \
+            constexpr int RPTV = 4, SV = 4;                   \
+            __VA_ARGS__;                                      \
+        } else {                                              \
+            constexpr int RPTV = 2, SV = 4;                   \
+            __VA_ARGS__;                                      \
+        }                                                     \
+    } while (0)
+
+// max that propagates NaN (so one comparison can screen several values)
+__device__ __forceinline__ float nanmax(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Cubic root of the RPT x VX values of one thread.  With the series solve and every
+// xi^2 <= fast2max, the series is evaluated without per-point checks and (when the
+// rounding guard is on) clamped with plain min/max: fast2max keeps |xi| <= 1 + 8 ulp,
+// where the exact root is within [-1, 1] to rounding, so this gives the same values
+// as the per-point path.  Otherwise every point takes cubic_root().
+template <typename T, int SOLVE, int N>
+__device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<T>& c) {
+    if (SOLVE == kSolveFex) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = xi[i];
+        return;
+    }
+    if (SOLVE == kSolveSeries) {
+        T x2[N];
+        T m = T(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            x2[i] = xi[i] * xi[i];
+            m = nanmax(m, x2[i]);
+        }
+        if (m <= c.fast2max) {
+            constexpr int NT = SeriesTerms<T>::value;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                T P = c.q[NT - 1];
+#pragma unroll
+                for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2[i], c.q[k]);
+                T th = xi[i] * P;
+                if (c.clamp) th = fmin(fmax(th, T(-1)), T(1));
+                out[i] = th;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = cubic_root<T, SOLVE>(xi[i], c);
+}
 
 template <typename T>
 struct Vec;

@@ -267,3 +267,48 @@ def test_tiled2d_bitwise_equals_naive(acs, shape, bc, dtype):
     assert np.array_equal(a.numpy(), b.numpy())
     if dtype == "f64":
         assert relerr(a.numpy(), oracle.run_fd(phi0, eps, dt, h, bc, 30)) <= 1e-12
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("dims,shape,bc,dtype", [(3, (37, 45, 132), BC_NEUMANN, "f32"), (3, (9, 70, 64), BC_PERIODIC, "f64"),
+                                                 (2, (150, 264), BC_DIRICHLET, "f32"), (2, (77, 130), BC_PERIODIC, "f64")],
+                         ids=str)
+def test_tile_variants_bitwise(acs, variant, dims, shape, bc, dtype):
+    h, eps, dt, phi0 = _problem(shape, bc, 90 + variant)
+    a = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    b = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    a.set_kernel(acs.ACS_KERNEL_TILED)
+    acs.check(acs.lib().acs_set_variant(a.ctx, variant, 7 if dims == 3 else 3))
+    b.set_kernel(acs.ACS_KERNEL_NAIVE)
+    a.set_state(phi0)
+    b.set_state(phi0)
+    a.step(21)
+    b.step(21)
+    assert np.array_equal(a.numpy(), b.numpy())
+
+
+def test_autotune_keeps_state_and_bits(acs, tmp_path, monkeypatch):
+    monkeypatch.setenv("ACS_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    import ctypes
+    shape = (96, 80, 128)
+    h, eps, dt, phi0 = _problem(shape, BC_NEUMANN, 5)
+    p32 = phi0.astype(np.float32)
+    a = acs.AllenCahn(shape, eps, dt, h, BC_NEUMANN, "f32")
+    a.set_state(p32)
+    us = ctypes.c_double()
+    acs.check(acs.lib().acs_autotune(a.ctx, ctypes.byref(us)))
+    assert us.value > 0
+    assert np.array_equal(a.numpy(), p32)          # candidates never write the state
+    assert (tmp_path / "tune.txt").read_text().strip()
+    b = acs.AllenCahn(shape, eps, dt, h, BC_NEUMANN, "f32")
+    b.set_kernel(acs.ACS_KERNEL_NAIVE)
+    b.set_state(p32)
+    a.step(12)
+    b.step(12)
+    assert np.array_equal(a.numpy(), b.numpy())
+    # a second context of the same class takes the cached choice without timing
+    c = acs.AllenCahn(shape, eps, dt, h, BC_NEUMANN, "f32")
+    c.set_state(p32)
+    c.step(12)
+    assert c.get_kernel() == a.get_kernel()
+    assert np.array_equal(c.numpy(), b.numpy())
