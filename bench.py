@@ -117,28 +117,25 @@ class ClockSampler:
 
 
 def _traffic_from_profile(kernel_tag: str):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if its
-    recorded source digest still matches the kernel source (else None)."""
+    """Per-launch DRAM bytes of the step kernel from the committed ncu record, if the
+    recorded digest of its sources still matches (else None: the kernel has changed)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    rows = {}
     with open(path) as f:
         for line in f:
-            if line.startswith("#") or not line.strip():
-                continue
             parts = line.split()
-            if len(parts) >= 4:
-                rows[parts[0]] = (parts[1], float(parts[2]), parts[3])
-    if kernel_tag not in rows:
-        return None
-    src_file, per_launch, digest = rows[kernel_tag]
-    src = os.path.join(ROOT, "paper_2312_07010_gb300", "csrc", src_file)
-    if not os.path.exists(src):
-        return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return per_launch if h == digest else None
+            if line.startswith("#") or len(parts) < 4 or parts[0] != kernel_tag:
+                continue
+            h = hashlib.sha256()
+            for src in parts[1].split(","):
+                fp = os.path.join(ROOT, "paper_2312_07010_gb300", "csrc", src)
+                if not os.path.exists(fp):
+                    return None
+                h.update(open(fp, "rb").read())
+            return float(parts[2]) if h.hexdigest()[:16] == parts[3] else None
+    return None
 
 
 def cpu_oracle_sample(budget_s: float = 12.0):
@@ -322,7 +319,8 @@ def main():
     launch_ms = ea.elapsed_time(eb) / (2 * reps)
     alg_bytes = 2 * 4 * w.numel * K
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
-    ktag = {P.ACS_KERNEL_NAIVE: "naive", P.ACS_KERNEL_TILED: "tiled", P.ACS_KERNEL_TEMPORAL: f"temporal{K}"}[kernel]
+    ktag = {P.ACS_KERNEL_NAIVE: "naive", P.ACS_KERNEL_TILED: f"tiled_v{variant}",
+            P.ACS_KERNEL_TEMPORAL: f"temporal{K}_v{variant}"}[kernel]
     traffic = _traffic_from_profile(f"step3d_f32_neumann_512_{ktag}")
 
     launches_per_step = (w.steps // K) + 2 * n_logs

@@ -182,7 +182,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 size_t state_bytes(const acs_ctx* c) { return (size_t)c->g.total * c->esize; }
 
 size_t off_partials(const acs_ctx* c) { return align_up(state_bytes(c)); }
-size_t off_result(const acs_ctx* c) { return off_partials(c) + align_up(sizeof(RedPartial) * kMaxRedBlocks); }
+size_t off_result(const acs_ctx* c) { return off_partials(c) + align_up(sizeof(RedPartial) * kMaxStreamParts); }
 size_t off_log(const acs_ctx* c) { return off_result(c) + kAlign; }
 size_t off_flags(const acs_ctx* c) { return off_log(c) + align_up(sizeof(double) * 2 * kLogCap); }
 size_t work_total(const acs_ctx* c) { return off_flags(c) + kAlign; }
@@ -307,6 +307,17 @@ static int check_err_flag(acs_ctx* c) {
 }
 
 static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, cudaStream_t st) {
+    if (c->dims == 3 && tiled_supported(c->dims, c->dtype, c->g)) {
+        // the TMA-streamed pipeline: vector loads, neighbours from registers and shuffles
+        int np = 0;
+        const cudaError_t e =
+            c->dtype == ACS_F32
+                ? launch_energy3d<float>(c->bc, (const float*)state, c->g, c->cf, c->err, c->partials, &np, st)
+                : launch_energy3d<double>(c->bc, (const double*)state, c->g, c->cd, c->err, c->partials, &np, st);
+        if (e == cudaSuccess) return launch_reduce_finish(c->partials, np, c->dims, c->eps * c->eps, c->h, out2, st);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+    }
     if (c->dtype == ACS_F32)
         return launch_reduce<float>(c->dims, c->bc, (const float*)state, c->g, c->eps * c->eps, c->h,
                                     c->partials, out2, st);

@@ -13,6 +13,7 @@ struct RedPartial {
     double bulk_s, bulk_c, link_s, link_c, mx, pad0, pad1, pad2;
 };
 constexpr int kMaxRedBlocks = 1024;
+constexpr int kMaxStreamParts = 16384;  // partials of the streamed energy kernels
 
 template <typename T>
 cudaError_t launch_step_naive(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c,
@@ -30,6 +31,14 @@ cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* d
                                  const Coef<T>& c, int* err, cudaStream_t st);
 bool tiled_supported(int dims, int dtype, const Geo& g);
 bool temporal_supported(int dims, int dtype, int depth, const Geo& g);
+
+// E_h and max |phi| with the TMA-streamed pipeline (3D, rows a multiple of 16 bytes);
+// cudaErrorNotSupported when it does not apply.
+template <typename T>
+cudaError_t launch_energy3d(int bc, const T* src, const Geo& g, const Coef<T>& c, int* err, RedPartial* part,
+                            int* nparts, cudaStream_t st);
+cudaError_t launch_reduce_finish(const RedPartial* part, int nparts, int dims, double eps2, double h, double* out2,
+                                 cudaStream_t st);
 
 // E_h and max |phi|: partials then a one-block finish writing {E_h, max} to out2.
 int reduce_blocks(const Geo& g);

@@ -17,47 +17,6 @@
 
 namespace acs {
 
-// ---------------------------------------------------------------- FP32 states
-// FP64 arithmetic runs at 1/57 of the FP32 rate on this GPU, so the FP32 path forms
-// every term exactly with error-free FP32 transformations (the build uses
-// -fmad=false, so nothing below is contracted): the difference q - p of two floats
-// is an exact pair (TwoSum), its square and p^2 are exact pairs up to the
-// negligible lo^2 term (TwoProduct via fma), and terms are accumulated into an
-// unevaluated float pair (hi, lo).  All terms are non-negative, so the pair keeps
-// about 2^-46 relative accuracy; every 32 points it is flushed into the FP64
-// compensated sum.
-
-struct F2 {
-    float hi, lo;
-};
-
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    return F2{s, (a - (s - bb)) + (b - bb)};
-}
-
-// acc += x (x >= 0 given as an unevaluated pair)
-__device__ __forceinline__ void f2_acc(F2& acc, float xh, float xl) {
-    const F2 t = two_sum(acc.hi, xh);
-    acc.hi = t.hi;
-    acc.lo = (acc.lo + t.lo) + xl;
-}
-
-// the exact square of (q - p), accumulated
-__device__ __forceinline__ void link_sq(F2& acc, float q, float p) {
-    const F2 d = two_sum(q, -p);
-    const float sq = d.hi * d.hi;
-    const float sql = __fmaf_rn(d.hi, d.hi, -sq) + 2.0f * d.hi * d.lo;
-    f2_acc(acc, sq, sql);
-}
-
-__device__ __forceinline__ void flush(F2& acc, CSum& sum) {
-    cadd(sum, (double)acc.hi);
-    cadd(sum, (double)acc.lo);
-    acc = F2{0.0f, 0.0f};
-}
-
 template <int BC>
 __device__ __forceinline__ void axis_links_f(F2& acc, float p, float up, int64_t c, int64_t n) {
     if (c < n - 1 || BC == ACS_BC_PERIODIC) link_sq(acc, up, p);  // `up` is the wrap neighbour at the end
@@ -97,14 +56,7 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g
             const T uz = D >= 3 ? src[z < g.nz - 1 ? i + g.sz : y * g.sy + x] : T(0);
             if (sizeof(T) == 4) {
                 const float pf = (float)p;
-                // (p^2 - 1)^2 exactly up to 2^-46: p^2 = s + sl, w = p^2 - 1 = wh + wl
-                const float s2 = pf * pf;
-                const float s2l = __fmaf_rn(pf, pf, -s2);
-                const F2 w = two_sum(s2, -1.0f);
-                const float wh = w.hi, wl = w.lo + s2l;
-                const float q = wh * wh;
-                const float ql = __fmaf_rn(wh, wh, -q) + 2.0f * wh * wl;
-                f2_acc(fb, q, ql);
+                bulk_sq(fb, pf);  // (p^2 - 1)^2 exactly up to 2^-46
                 const float ap = fabsf(pf);
                 mx = (ap > mx || ap != ap) ? ap : mx;
                 axis_links_f<BC>(fl, pf, (float)ux, x, g.nx);
@@ -212,5 +164,11 @@ cudaError_t launch_reduce(int dims, int bc, const T* src, const Geo& g, double e
 
 template cudaError_t launch_reduce<float>(int, int, const float*, const Geo&, double, double, RedPartial*, double*, cudaStream_t);
 template cudaError_t launch_reduce<double>(int, int, const double*, const Geo&, double, double, RedPartial*, double*, cudaStream_t);
+
+cudaError_t launch_reduce_finish(const RedPartial* part, int nparts, int dims, double eps2, double h, double* out2,
+                                 cudaStream_t st) {
+    k_reduce_finish<<<1, 256, 0, st>>>(part, nparts, std::pow(h, (double)dims), 0.5 * eps2 / (h * h), out2);
+    return cudaGetLastError();
+}
 
 }  // namespace acs

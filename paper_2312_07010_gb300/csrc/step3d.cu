@@ -20,10 +20,10 @@
 
 namespace acs {
 
-template <typename T, int BC, int SOLVE, int RPT, int SS>
+template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
 __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src,
                                                 T* __restrict__ dst, Geo g, Coef<T> c, int ntx, int zchunk,
-                                                int* err) {
+                                                int* err, RedPartial* part) {
     using TT = Tile3<T, RPT, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
     const bool xlo = gx == 0, xhi = gx + VX == nx;
     const bool vecok = gx + VX <= nx;
     T* o = dst + (int64_t)z0 * sz + (int64_t)gy0 * sy + gx;
+    EnergyAcc<T> eacc;
 
     // One plane: zm / cz / zp are this thread's values at z-1, z, z+1.
     auto plane = [&](int z, T (&zm)[RPT][VX], T (&cz)[RPT][VX], T (&zp)[RPT][VX]) {
@@ -142,6 +143,25 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
                 if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[rowoff + nx - 1];
                 if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[rowoff];
             }
+            if (MODE == kModeEnergy) {
+                // E_h and max-norm of this (input) state: the forward link of every
+                // unknown along x, y, z (ghost-ruled neighbours as for the step), plus
+                // the links of the first unknowns to the zero Dirichlet boundary
+                if (gyr < ny) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        if (gx + v >= nx) continue;
+                        const T p = cz[rr][v];
+                        eacc.point(p, v == VX - 1 ? right : cz[rr][v + 1], yp[v], zp[rr][v]);
+                        if (BC == ACS_BC_DIRICHLET) {
+                            if (gx + v == 0) eacc.ghost_link(p);
+                            if (gyr == 0) eacc.ghost_link(p);
+                            if (z == 0) eacc.ghost_link(p);
+                        }
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
                 const T xm = v == 0 ? left : cz[rr][v - 1];
@@ -149,6 +169,13 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
                 const T s = nsum(zm[rr][v], zp[rr][v], ym[v], yp[v], xm, xp);
                 xi[rr * VX + v] = predictor(cz[rr][v], s, c);
             }
+        }
+        if (MODE == kModeEnergy) {
+            eacc.plane_done();
+            failed = __syncthreads_or(!ok);
+            if (!failed && tid == 0 && z + S <= z1) issue(z + S);
+            if (!failed) last_issued = max(last_issued, min(z + S, z1));
+            return;
         }
         T out[NP];
         roots<T, SOLVE, NP>(xi, out, c);
@@ -183,6 +210,7 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
         plane(z, zm, cz, zq);
         if (!failed && z + 1 < z1) plane(z + 1, cz, zq, zm);
     }
+    if (MODE == kModeEnergy) energy_block_write(eacc, part + (blockIdx.y * gridDim.x + blockIdx.x));
     if (failed) {
         // record the timeout, then let the newest load of every slot land (bounded)
         // before the CTA's shared memory goes away
@@ -218,9 +246,9 @@ static int choose_zchunk(int64_t tiles, int64_t nz, int resident) {
     return best;
 }
 
-template <typename T, int RPT, int SS>
+template <typename T, int RPT, int SS, int MODE>
 static cudaError_t launch3d_variant(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zchunk,
-                                    int* err, cudaStream_t st) {
+                                    int* err, RedPartial* part, int* nparts, cudaStream_t st) {
     using TT = Tile3<T, RPT, SS>;
     CUtensorMap map;
     const uint64_t dims[3] = {(uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz};
@@ -231,8 +259,8 @@ static cudaError_t launch3d_variant(int bc, const T* src, T* dst, const Geo& g, 
     if ((int64_t)ntx * nty > 0x7fffffff) return cudaErrorNotSupported;
     cudaError_t e = cudaSuccess;
     ACS_SOLVE_DISPATCH(c.solve, SV, {
-        auto kern = bc == 0 ? k_step3d<T, 0, SV, RPT, SS>
-                            : (bc == 1 ? k_step3d<T, 1, SV, RPT, SS> : k_step3d<T, 2, SV, RPT, SS>);
+        auto kern = bc == 0 ? k_step3d<T, 0, SV, RPT, SS, MODE>
+                            : (bc == 1 ? k_step3d<T, 1, SV, RPT, SS, MODE> : k_step3d<T, 2, SV, RPT, SS, MODE>);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);
         if (e == cudaSuccess && zchunk <= 0) {
             int dev = 0, sms = 0, per_sm = 0;
@@ -243,9 +271,12 @@ static cudaError_t launch3d_variant(int bc, const T* src, T* dst, const Geo& g, 
         }
         const int nzc = (int)((g.nz + zchunk - 1) / zchunk);
         if (e == cudaSuccess && nzc > 65535) e = cudaErrorNotSupported;
+        if (e == cudaSuccess && MODE == kModeEnergy && (int64_t)ntx * nty * nzc > kMaxStreamParts)
+            e = cudaErrorNotSupported;
+        if (nparts) *nparts = ntx * nty * nzc;
         if (e == cudaSuccess)
             kern<<<dim3((unsigned)(ntx * nty), (unsigned)nzc), dim3(32, 8), TT::SMEM, st>>>(map, src, dst, g, c, ntx,
-                                                                                              zchunk, err);
+                                                                                              zchunk, err, part);
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -255,9 +286,23 @@ template <typename T>
 cudaError_t launch_step3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant, int zchunk,
                           int* err, cudaStream_t st) {
     cudaError_t e = cudaErrorInvalidValue;
-    ACS_TILE_VARIANT_DISPATCH(variant, RPTV, SV, (e = launch3d_variant<T, RPTV, SV>(bc, src, dst, g, c, zchunk, err, st)));
+    ACS_TILE_VARIANT_DISPATCH(variant, RPTV, SV,
+                              (e = launch3d_variant<T, RPTV, SV, kModeStep>(bc, src, dst, g, c, zchunk, err, nullptr,
+                                                                          nullptr, st)));
     return e;
 }
+
+// E_h / max-norm of `src` with the streamed pipeline: per-CTA partials into `part`
+// (at most kMaxStreamParts), their count in *nparts.
+template <typename T>
+cudaError_t launch_energy3d(int bc, const T* src, const Geo& g, const Coef<T>& c, int* err, RedPartial* part,
+                            int* nparts, cudaStream_t st) {
+    return launch3d_variant<T, 2, 6, kModeEnergy>(bc, src, nullptr, g, c, 0, err, part, nparts, st);
+}
+template cudaError_t launch_energy3d<float>(int, const float*, const Geo&, const Coef<float>&, int*, RedPartial*,
+                                            int*, cudaStream_t);
+template cudaError_t launch_energy3d<double>(int, const double*, const Geo&, const Coef<double>&, int*, RedPartial*,
+                                             int*, cudaStream_t);
 
 template cudaError_t launch_step3d<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int, int*,
                                           cudaStream_t);

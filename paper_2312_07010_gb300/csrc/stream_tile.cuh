@@ -2,7 +2,8 @@
 // kernels (3D: xy tiles streamed through z; 2D: x tiles streamed through row blocks).
 #pragma once
 
-#include "acs_device.cuh"
+#include "acs_kernels.cuh"
+#include "acs_reduce.cuh"
 
 namespace acs {
 
@@ -29,6 +30,95 @@ struct Tile3 {
     static_assert(BW <= 256 && BH <= 256, "TMA box dimensions");
 };
 
+// max that propagates NaN (so one comparison can screen several values)
+__device__ __forceinline__ float nanmax(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Modes of the streamed kernels: one step, or the energy / max-norm reduction of the
+// input state (same pipeline, the step's ghost-ruled forward neighbours).
+enum StreamMode : int { kModeStep = 0, kModeEnergy = 1 };
+
+// Per-thread E_h / max-norm accumulation for the streamed kernels.  FP32 states: terms
+// are formed exactly with error-free transformations into float pairs (acs_reduce.cuh)
+// and folded into FP64 every 4 planes (at most 128 terms per pair: about 2^-41 relative
+// accumulation error); FP64 states: plain FP64 sums.  The bulk sum is of (p^2 - 1)^2
+// (the 1/4 is applied by the finishing kernel), the link sum of squared differences.
+template <typename T>
+struct EnergyAcc;
+template <>
+struct EnergyAcc<float> {
+    F2 fb{0.0f, 0.0f}, fl{0.0f, 0.0f};
+    double db = 0.0, dl = 0.0, mx = 0.0;
+    float fmx = 0.0f;
+    int planes = 0;
+    __device__ __forceinline__ void point(float p, float xn, float yn, float zn) {
+        bulk_sq(fb, p);
+        link_sq(fl, xn, p);
+        link_sq(fl, yn, p);
+        link_sq(fl, zn, p);
+        fmx = nanmax(fmx, fabsf(p));
+    }
+    __device__ __forceinline__ void ghost_link(float p) { link_sq(fl, 0.0f, p); }
+    __device__ __forceinline__ void fold() {
+        db += (double)fb.hi + (double)fb.lo;
+        dl += (double)fl.hi + (double)fl.lo;
+        fb = F2{0.0f, 0.0f};
+        fl = F2{0.0f, 0.0f};
+    }
+    __device__ __forceinline__ void plane_done() {
+        if (++planes == 4) { fold(); planes = 0; }
+    }
+    __device__ __forceinline__ void finish() {
+        fold();
+        mx = (double)fmx;
+    }
+};
+template <>
+struct EnergyAcc<double> {
+    double db = 0.0, dl = 0.0, mx = 0.0;
+    __device__ __forceinline__ void point(double p, double xn, double yn, double zn) {
+        const double w = fma(p, p, -1.0);
+        db = fma(w, w, db);
+        const double a = xn - p, b = yn - p, c = zn - p;
+        dl = fma(a, a, dl);
+        dl = fma(b, b, dl);
+        dl = fma(c, c, dl);
+        mx = nanmax(mx, fabs(p));
+    }
+    __device__ __forceinline__ void ghost_link(double p) { dl = fma(p, p, dl); }
+    __device__ __forceinline__ void plane_done() {}
+    __device__ __forceinline__ void finish() {}
+};
+
+// Block-combine the per-thread sums (thread 0 writes the block's partial).
+template <typename T>
+__device__ __forceinline__ void energy_block_write(EnergyAcc<T>& acc, RedPartial* out) {
+    acc.finish();
+    CSum b{acc.db, 0.0}, l{acc.dl, 0.0};
+    double m = acc.mx;
+    for (int off = 16; off > 0; off >>= 1) {
+        b = cmerge(b, shfl_down(b, off));
+        l = cmerge(l, shfl_down(l, off));
+        m = nmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    }
+    __shared__ CSum sb[32], sl[32];
+    __shared__ double sm[32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) { sb[warp] = b; sl[warp] = l; sm[warp] = m; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < nw; ++w) { b = cmerge(b, sb[w]); l = cmerge(l, sl[w]); m = nmax(m, sm[w]); }
+        *out = RedPartial{b.s, b.c, l.s, l.c, m, 0.0, 0.0, 0.0};
+    }
+}
+
 // Tile variants offered to the autotuner: (rows per thread, ring slots).
 constexpr int kNumTileVariants = 3;
 #define ACS_TILE_VARIANT_DISPATCH(var, RPTV, SV, ...)          \
@@ -44,14 +134,6 @@ constexpr int kNumTileVariants = 3;
             __VA_ARGS__;                                      \
         }                                                     \
     } while (0)
-
-// max that propagates NaN (so one comparison can screen several values)
-__device__ __forceinline__ float nanmax(float a, float b) {
-    float r;
-    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
 
 // Cubic root of the RPT x VX values of one thread.  With the series solve and every
 // xi^2 <= fast2max, the series is evaluated without per-point checks and (when the

@@ -75,7 +75,8 @@ def test_fp32_parity_200_steps(acs, shape, bc):
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
-@pytest.mark.parametrize("shape", [(9,), (5, 7), (33, 65), (7, 6, 5), (40, 33, 20)], ids=str)
+@pytest.mark.parametrize("shape", [(9,), (5, 7), (33, 65), (7, 6, 5), (40, 33, 20), (9, 20, 136), (64, 64, 64),
+                                   (1, 3, 8)], ids=str)
 def test_energy_and_maxnorm_parity(acs, shape, bc, dtype):
     h, eps, dt, phi0 = _problem(shape, bc, 41 + len(shape) + bc)
     s = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
