@@ -313,3 +313,24 @@ def test_autotune_keeps_state_and_bits(acs, tmp_path, monkeypatch):
     c.step(12)
     assert c.get_kernel() == a.get_kernel()
     assert np.array_equal(c.numpy(), b.numpy())
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_fig4_schemes_match_oracle(acs, scheme):
+    """Both schemes of the Fig. 4 comparison (lambda = 0.45, dx = 1/32, dt = 1/5) on the GPU
+    follow the oracle step for step; FEX-FD exceeds |phi| = 1, RLB-MIE-FD does not."""
+    lam, h, dt = 0.45, 1 / 32, 0.2
+    eps = math.sqrt(lam * h * h / dt)
+    N = round(3 / h)
+    x = -0.5 + h * np.arange(N + 1)
+    phi = 0.5 * (1 - np.tanh(x / (2 * math.sqrt(2) * eps)))
+    s = acs.AllenCahn((N + 1,), eps, dt, h, BC_NEUMANN, "f64")
+    s.set_scheme(scheme)
+    s.set_state(phi)
+    worst = 0.0
+    for _ in range(50):
+        s.step(1)
+        phi = oracle.step_fd(phi, eps, dt, h, BC_NEUMANN, scheme=scheme)
+        assert relerr(s.numpy(), phi) <= 1e-12
+        worst = max(worst, s.maxnorm())
+    assert (worst > 1.0) == (scheme == 1)

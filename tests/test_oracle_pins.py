@@ -323,3 +323,31 @@ def test_grad_vs_central_differences(orc, bc):
     assert ge2 == pytest.approx(fde, rel=1e-5)
     g0b, ge2b = orc.grad(phi0, eps, dt, h, bc, steps, gT, checkpoint_every=0)
     assert np.array_equal(g0, g0b) and ge2 == ge2b
+
+
+def test_fex_fd_loses_maximum_principle_where_rlb_mie_fd_keeps_it(orc):
+    """Fig. 4 / Remark 2: traveling wave, lambda = 0.45, dx = 1/32, dt = 1/5.  The
+    RLB-MIE-FD scheme keeps |phi| <= 1 and a non-increasing energy and stays closer to
+    the exact wave; the fully explicit FEX-FD scheme exceeds 1.  (The magnitudes of
+    Table 1 do not reproduce; the qualitative contrast does.)"""
+    lam, h, dt = 0.45, 1 / 32, 0.2
+    eps = math.sqrt(lam * h * h / dt)
+    se = 3 * eps / math.sqrt(2)
+    T = 1 / se
+    N = round(3 / h)
+    x = -0.5 + h * np.arange(N + 1)
+    phi0 = 0.5 * (1 - np.tanh(x / (2 * math.sqrt(2) * eps)))
+    exact = 0.5 * (1 - np.tanh((x - se * T) / (2 * math.sqrt(2) * eps)))
+    res = {}
+    for scheme in (orc.SCHEME_RLB_MIE_FD, orc.SCHEME_FEX_FD):
+        p = phi0.copy()
+        E = [orc.energy(p, eps, dt, h, 1)]
+        M = [orc.maxnorm(p)]
+        for _ in range(math.floor(T / dt)):
+            p = orc.step_fd(p, eps, dt, h, 1, scheme=scheme)
+            E.append(orc.energy(p, eps, dt, h, 1))
+            M.append(orc.maxnorm(p))
+        res[scheme] = (max(M), np.all(np.diff(E) <= 1e-15), float(np.abs(p - exact).max()))
+    assert res[0][0] <= 1.0 and res[0][1]
+    assert res[1][0] > 1.0
+    assert res[0][2] < res[1][2]
