@@ -209,10 +209,14 @@ def main():
     ap.add_argument("--depth", type=int, default=1)
     ap.add_argument("--profile", action="store_true",
                     help="only set up the 512^3 workload and run --steps time steps (for ncu captures)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="only set up the 256-instance batched workload and run --steps time steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch:
+        return profile_batch(args)
 
     import numpy as np
     import torch
@@ -351,6 +355,22 @@ def main():
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
+    return 0
+
+
+def profile_batch(args):
+    import numpy as np
+    import torch
+
+    import paper_2312_07010_gb300 as P
+    from workloads import batched_instances
+    inst = batched_instances()
+    b = P.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+                [i.bc for i in inst], "f32")
+    b.set_states([i.phi0().astype(np.float32) for i in inst])
+    b.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "batched", "instances": len(inst), "time_steps": args.steps}))
     return 0
 
 

@@ -195,6 +195,15 @@ ACS_API int acs_energy(acs_ctx* ctx, double* out_host);
  * Synchronizes the stream; ACS_E_NONFINITE (value still written) for NaN/Inf. */
 ACS_API int acs_maxnorm(acs_ctx* ctx, double* out_host);
 
+/*
+ * acs_phase_volume -- the volume (area in 2D, length in 1D) of the phase phi > 0,
+ * measured as h^d sum_i (1 + phi_i) / 2 over the unknowns: the quantity behind the
+ * radius of the shrinking circle / sphere of Sec. IV.B.2 (motion by mean curvature,
+ * R(t) = sqrt(R0^2 - 2 eps^2 t) in 2D, sqrt(R0^2 - 4 eps^2 t) in 3D).  FP64, compensated;
+ * synchronizes the stream.
+ */
+ACS_API int acs_phase_volume(acs_ctx* ctx, double* out_host);
+
 /* Both reductions, written as {E_h, max|phi|} to two doubles of device memory,
  * asynchronously (no synchronization). */
 ACS_API int acs_observe_async(acs_ctx* ctx, double* d_out2);

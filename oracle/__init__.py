@@ -157,6 +157,13 @@ def maxnorm(phi: np.ndarray) -> float:
     return float(lib().acs_oracle_maxnorm(d, n, _ptr(p)))
 
 
+def phase_volume(phi: np.ndarray, h: float) -> float:
+    """Volume of the phase phi > 0 measured as h^d sum (1 + phi)/2 (the radius of Sec. IV.B.2's
+    shrinking circle / sphere follows from it); math.fsum makes the sum exact before rounding."""
+    p = _f64(phi)
+    return float(h ** p.ndim * math.fsum(((1.0 + p) / 2.0).ravel()))
+
+
 def adjoint_step(phi_n: np.ndarray, phi_np1: np.ndarray, adj_np1: np.ndarray, eps: float,
                  dt: float, h: float, bc: int) -> Tuple[np.ndarray, float]:
     """(dL/dphi^n, this step's dL/d(eps^2)) from dL/dphi^{n+1} for one step of Eq. (IE-FD)."""

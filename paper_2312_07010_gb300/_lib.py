@@ -45,6 +45,7 @@ SIGNATURES = {
     "acs_steps_done": (_i64, [_vp]),
     "acs_energy": (_c.c_int, [_vp, _dp]),
     "acs_maxnorm": (_c.c_int, [_vp, _dp]),
+    "acs_phase_volume": (_c.c_int, [_vp, _dp]),
     "acs_observe_async": (_c.c_int, [_vp, _vp]),
     "acs_run_logged": (_c.c_int, [_vp, _i64, _i64, _dp, _dp]),
     "acs_grad_work_bytes": (_c.c_size_t, [_vp, _i64, _i64]),

@@ -307,13 +307,19 @@ static int check_err_flag(acs_ctx* c) {
 }
 
 static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, cudaStream_t st) {
-    if (c->dims == 3 && tiled_supported(c->dims, c->dtype, c->g)) {
+    const bool rows16 = (c->g.nx * (int64_t)c->esize) % 16 == 0;
+    if ((c->dims == 3 || c->dims == 2) && rows16 && tiled_supported(c->dims, c->dtype, c->g)) {
         // the TMA-streamed pipeline: vector loads, neighbours from registers and shuffles
         int np = 0;
-        const cudaError_t e =
-            c->dtype == ACS_F32
-                ? launch_energy3d<float>(c->bc, (const float*)state, c->g, c->cf, c->err, c->partials, &np, st)
-                : launch_energy3d<double>(c->bc, (const double*)state, c->g, c->cd, c->err, c->partials, &np, st);
+        cudaError_t e;
+        if (c->dims == 3)
+            e = c->dtype == ACS_F32
+                    ? launch_energy3d<float>(c->bc, (const float*)state, c->g, c->cf, c->err, c->partials, &np, st)
+                    : launch_energy3d<double>(c->bc, (const double*)state, c->g, c->cd, c->err, c->partials, &np, st);
+        else
+            e = c->dtype == ACS_F32
+                    ? launch_energy2d<float>(c->bc, (const float*)state, c->g, c->cf, c->err, c->partials, &np, st)
+                    : launch_energy2d<double>(c->bc, (const double*)state, c->g, c->cd, c->err, c->partials, &np, st);
         if (e == cudaSuccess) return launch_reduce_finish(c->partials, np, c->dims, c->eps * c->eps, c->h, out2, st);
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
@@ -565,6 +571,24 @@ ACS_API int acs_maxnorm(acs_ctx* c, double* out_host) {
     int rc = observe_host(c, nullptr, &m);
     *out_host = m;
     return rc;
+}
+
+ACS_API int acs_phase_volume(acs_ctx* c, double* out_host) {
+    if (!c || !out_host) return ACS_E_INVAL;
+    if (!c->bound) return ACS_E_STATE;
+    cudaError_t e = c->dtype == ACS_F32
+                        ? launch_phase_volume<float>((const float*)c->phi, c->g.total, c->dims, c->h, c->partials,
+                                                     c->result, c->stream)
+                        : launch_phase_volume<double>((const double*)c->phi, c->g.total, c->dims, c->h, c->partials,
+                                                      c->result, c->stream);
+    if (e != cudaSuccess) return ACS_E_CUDA;
+    double v = 0.0;
+    if (cudaMemcpyAsync(&v, c->result, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return ACS_E_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;
+    if (int rc = check_err_flag(c)) return rc;
+    *out_host = v;
+    return std::isfinite(v) ? ACS_OK : ACS_E_NONFINITE;
 }
 
 ACS_API int acs_run_logged(acs_ctx* c, int64_t n_steps, int64_t every, double* h_energy, double* h_maxnorm) {

@@ -37,8 +37,16 @@ bool temporal_supported(int dims, int dtype, int depth, const Geo& g);
 template <typename T>
 cudaError_t launch_energy3d(int bc, const T* src, const Geo& g, const Coef<T>& c, int* err, RedPartial* part,
                             int* nparts, cudaStream_t st);
+template <typename T>
+cudaError_t launch_energy2d(int bc, const T* src, const Geo& g, const Coef<T>& c, int* err, RedPartial* part,
+                            int* nparts, cudaStream_t st);
 cudaError_t launch_reduce_finish(const RedPartial* part, int nparts, int dims, double eps2, double h, double* out2,
                                  cudaStream_t st);
+
+// h^d sum (1 + phi)/2 into out (scratch: kMaxRedBlocks * 16 bytes).
+template <typename T>
+cudaError_t launch_phase_volume(const T* src, int64_t n, int dims, double h, void* scratch, double* out,
+                                cudaStream_t st);
 
 // E_h and max |phi|: partials then a one-block finish writing {E_h, max} to out2.
 int reduce_blocks(const Geo& g);

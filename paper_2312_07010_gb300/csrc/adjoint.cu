@@ -157,10 +157,10 @@ __global__ void __launch_bounds__(256) k_adjoint2d(const T* __restrict__ phin, c
             const int r = 2 * w + rr;
             const int gy = y0 + r;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int cx = lane + 32 * k;
+            for (int k = 0; k < TT::VX; ++k) {
+                const int cx = lane + 32 * k;  // tile column (staged column VX + cx)
                 const int gx = x0 + cx;
-                const int i = (r + 1) * TT::BW + (cx + 1);
+                const int i = (r + 1) * TT::BW + TT::VX + cx;
                 const T mu = M[i], p = P[i];
                 const T smu = nsum(M[i - TT::BW], M[i + TT::BW], M[i - 1], M[i + 1]);
                 const T sphi = nsum(P[i - TT::BW], P[i + TT::BW], P[i - 1], P[i + 1]);

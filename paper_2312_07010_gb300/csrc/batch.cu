@@ -272,7 +272,7 @@ ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, con
         if (!std::isfinite(eps[i]) || !std::isfinite(dt[i]) || !std::isfinite(h[i])) return ACS_E_INVAL;
         if (eps[i] < 0 || !(h[i] > 0) || !(dt[i] > 0) || !(dt[i] < 2) || bc[i] < 0 || bc[i] > 2) return ACS_E_INVAL;
         numel += n[i] * n[i];
-        tiles += ((n[i] + 127) / 128) * ((n[i] + 15) / 16);
+        tiles += ((n[i] + 63) / 64) * ((n[i] + 15) / 16);  // the FP64 tile (64 x 16) bounds both
         if (numel > (int64_t(1) << 40) || tiles > 0x7fffffff) return ACS_E_INVAL;
     }
     acs_batch* b = new (std::nothrow) acs_batch();

@@ -171,4 +171,61 @@ cudaError_t launch_reduce_finish(const RedPartial* part, int nparts, int dims, d
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- phase volume
+// sum_i phi_i over the unknowns (the volume is h^d (N + sum phi) / 2).  FP32 states:
+// exact float-pair accumulation (TwoSum) folded into FP64 every 64 values; FP64
+// states: plain FP64 per thread.  Partials are compensated and combined in a fixed
+// order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_phase_sum(const T* __restrict__ src, int64_t n, CSum* part) {
+    CSum sum{0.0, 0.0};
+    F2 f{0.0f, 0.0f};
+    double d = 0.0;
+    int pending = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (sizeof(T) == 4) {
+            const F2 t = two_sum(f.hi, (float)src[i]);
+            f.hi = t.hi;
+            f.lo += t.lo;
+            if (++pending == 64) {
+                cadd(sum, (double)f.hi);
+                cadd(sum, (double)f.lo);
+                f = F2{0.0f, 0.0f};
+                pending = 0;
+            }
+        } else {
+            d += (double)src[i];
+        }
+    }
+    if (sizeof(T) == 4) {
+        cadd(sum, (double)f.hi);
+        cadd(sum, (double)f.lo);
+    } else {
+        cadd(sum, d);
+    }
+    __shared__ CSum scratch[32];
+    sum = block_csum(sum, scratch);
+    if (threadIdx.x == 0) part[blockIdx.x] = sum;
+}
+
+__global__ void k_phase_finish(const CSum* part, int nparts, int64_t n, double hd, double* out) {
+    CSum s{0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s = cmerge(s, part[i]);
+    __shared__ CSum scratch[32];
+    s = block_csum(s, scratch);
+    if (threadIdx.x == 0) out[0] = hd * 0.5 * ((double)n + (s.s + s.c));
+}
+
+template <typename T>
+cudaError_t launch_phase_volume(const T* src, int64_t n, int dims, double h, void* scratch, double* out,
+                                cudaStream_t st) {
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (n + 255) / 256));
+    CSum* part = reinterpret_cast<CSum*>(scratch);
+    k_phase_sum<T><<<nb, 256, 0, st>>>(src, n, part);
+    k_phase_finish<<<1, 256, 0, st>>>(part, nb, n, std::pow(h, (double)dims), out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_phase_volume<float>(const float*, int64_t, int, double, void*, double*, cudaStream_t);
+template cudaError_t launch_phase_volume<double>(const double*, int64_t, int, double, void*, double*, cudaStream_t);
+
 }  // namespace acs

@@ -14,10 +14,10 @@
 
 namespace acs {
 
-template <typename T, int BC, int SOLVE, int RPT, int SS>
+template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
 __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUtensorMap tmap,
                                                     const T* __restrict__ src, T* __restrict__ dst, Geo g,
-                                                    Coef<T> c, int ybchunk, int* err) {
+                                                    Coef<T> c, int ybchunk, int* err, RedPartial* part) {
     using TT = Tile3<T, RPT, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
     const bool xlo = gx == 0, xhi = gx + VX == nx;
     const bool vecok = gx + VX <= nx;
     bool failed = false;
+    EnergyAcc<T> eacc;
     for (int b = b0; b < b1 && !failed; ++b) {
         const int k = b - b0;
         const bool ok = mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
@@ -108,12 +109,38 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
                 if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[(int64_t)gyr * sy + nx - 1];
                 if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[(int64_t)gyr * sy];
             }
+            if (MODE == kModeEnergy) {
+                // forward links along x and y (ghost-ruled as for the step) and the
+                // links of the first unknowns to the zero Dirichlet boundary
+                if (gyr < ny) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        if (gx + v >= nx) continue;
+                        const T p = cz[rr][v];
+                        eacc.point2(p, v == VX - 1 ? right : cz[rr][v + 1], yp[v]);
+                        if (BC == ACS_BC_DIRICHLET) {
+                            if (gx + v == 0) eacc.ghost_link(p);
+                            if (gyr == 0) eacc.ghost_link(p);
+                        }
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
                 const T xm = v == 0 ? left : cz[rr][v - 1];
                 const T xp = v == VX - 1 ? right : cz[rr][v + 1];
                 xi[rr * VX + v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
             }
+        }
+        if (MODE == kModeEnergy) {
+            eacc.plane_done();
+            failed = __syncthreads_or(!ok);
+            if (!failed && tid == 0 && b + S < b1) {
+                issue(b + S);
+                last_issued = b + S;
+            }
+            continue;
         }
         T out[NP];
         roots<T, SOLVE, NP>(xi, out, c);
@@ -135,6 +162,7 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
             last_issued = b + S;
         }
     }
+    if (MODE == kModeEnergy) energy_block_write(eacc, part + (blockIdx.y * gridDim.x + blockIdx.x));
     if (failed) {
         if (tid == 0) {
             atomicExch(err, 1);
@@ -152,9 +180,9 @@ bool step2d_tma_supported(int dtype, const Geo& g) {
     return g.nz == 1 && (g.nx * esize) % 16 == 0 && g.nx < (1 << 30) && g.ny < (1 << 30);
 }
 
-template <typename T, int RPT, int SS>
+template <typename T, int RPT, int SS, int MODE>
 static cudaError_t launch2d_variant(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ybchunk,
-                                    int* err, cudaStream_t st) {
+                                    int* err, RedPartial* part, int* nparts, cudaStream_t st) {
     using TT = Tile3<T, RPT, SS>;
     CUtensorMap map;
     const uint64_t dims[2] = {(uint64_t)g.nx, (uint64_t)g.ny};
@@ -170,14 +198,16 @@ static cudaError_t launch2d_variant(int bc, const T* src, T* dst, const Geo& g, 
     }
     const int nchunks = (nyb + ybchunk - 1) / ybchunk;
     if (nchunks > 65535) return cudaErrorNotSupported;
+    if (MODE == kModeEnergy && (int64_t)ntx * nchunks > kMaxStreamParts) return cudaErrorNotSupported;
+    if (nparts) *nparts = ntx * nchunks;
     cudaError_t e = cudaSuccess;
     ACS_SOLVE_DISPATCH(c.solve, SV, {
-        auto kern = bc == 0 ? k_step2d_tma<T, 0, SV, RPT, SS>
-                            : (bc == 1 ? k_step2d_tma<T, 1, SV, RPT, SS> : k_step2d_tma<T, 2, SV, RPT, SS>);
+        auto kern = bc == 0 ? k_step2d_tma<T, 0, SV, RPT, SS, MODE>
+                            : (bc == 1 ? k_step2d_tma<T, 1, SV, RPT, SS, MODE> : k_step2d_tma<T, 2, SV, RPT, SS, MODE>);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);
         if (e == cudaSuccess)
             kern<<<dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), TT::SMEM, st>>>(map, src, dst, g, c, ybchunk,
-                                                                                        err);
+                                                                                        err, part);
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -188,9 +218,20 @@ cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const 
                               int ybchunk, int* err, cudaStream_t st) {
     cudaError_t e = cudaErrorInvalidValue;
     ACS_TILE_VARIANT_DISPATCH(variant, RPTV, SV,
-                              (e = launch2d_variant<T, RPTV, SV>(bc, src, dst, g, c, ybchunk, err, st)));
+                              (e = launch2d_variant<T, RPTV, SV, kModeStep>(bc, src, dst, g, c, ybchunk, err, nullptr,
+                                                                          nullptr, st)));
     return e;
 }
+
+template <typename T>
+cudaError_t launch_energy2d(int bc, const T* src, const Geo& g, const Coef<T>& c, int* err, RedPartial* part,
+                            int* nparts, cudaStream_t st) {
+    return launch2d_variant<T, 2, 6, kModeEnergy>(bc, src, nullptr, g, c, 0, err, part, nparts, st);
+}
+template cudaError_t launch_energy2d<float>(int, const float*, const Geo&, const Coef<float>&, int*, RedPartial*,
+                                            int*, cudaStream_t);
+template cudaError_t launch_energy2d<double>(int, const double*, const Geo&, const Coef<double>&, int*, RedPartial*,
+                                             int*, cudaStream_t);
 
 template cudaError_t launch_step2d_tma<float>(int, const float*, float*, const Geo&, const Coef<float>&, int, int,
                                               int*, cudaStream_t);

@@ -62,6 +62,12 @@ struct EnergyAcc<float> {
         link_sq(fl, zn, p);
         fmx = nanmax(fmx, fabsf(p));
     }
+    __device__ __forceinline__ void point2(float p, float xn, float yn) {
+        bulk_sq(fb, p);
+        link_sq(fl, xn, p);
+        link_sq(fl, yn, p);
+        fmx = nanmax(fmx, fabsf(p));
+    }
     __device__ __forceinline__ void ghost_link(float p) { link_sq(fl, 0.0f, p); }
     __device__ __forceinline__ void fold() {
         db += (double)fb.hi + (double)fb.lo;
@@ -87,6 +93,14 @@ struct EnergyAcc<double> {
         dl = fma(a, a, dl);
         dl = fma(b, b, dl);
         dl = fma(c, c, dl);
+        mx = nanmax(mx, fabs(p));
+    }
+    __device__ __forceinline__ void point2(double p, double xn, double yn) {
+        const double w = fma(p, p, -1.0);
+        db = fma(w, w, db);
+        const double a = xn - p, b = yn - p;
+        dl = fma(a, a, dl);
+        dl = fma(b, b, dl);
         mx = nanmax(mx, fabs(p));
     }
     __device__ __forceinline__ void ghost_link(double p) { dl = fma(p, p, dl); }

@@ -146,6 +146,12 @@ class AllenCahn:
             check(rc, "acs_maxnorm")
         return v.value
 
+    def phase_volume(self) -> float:
+        """h^d sum (1 + phi) / 2: the volume of the phase phi > 0 (acs_phase_volume)."""
+        v = ctypes.c_double()
+        check(self.L.acs_phase_volume(self.ctx, ctypes.byref(v)), "acs_phase_volume")
+        return v.value
+
     def observe_async(self, out2: torch.Tensor) -> None:
         """{E_h, max|phi|} into a 2-element float64 CUDA tensor, no synchronization."""
         check(self.L.acs_observe_async(self.ctx, ctypes.c_void_p(out2.data_ptr())), "acs_observe_async")

@@ -42,7 +42,8 @@ def test_batch_equals_standalone_fp32(acs, steps):
         s.set_state(phi0[k])
         s.step(steps)
         assert np.array_equal(got[k], s.numpy()), k
-        assert E[k] == s.energy() and M[k] == s.maxnorm()
+        # states are bit-identical; the reductions may sum in another order
+        assert E[k] == pytest.approx(s.energy(), rel=1e-12) and M[k] == s.maxnorm()
 
 
 def test_batch_fp64_vs_oracle(acs):

@@ -351,3 +351,30 @@ def test_fex_fd_loses_maximum_principle_where_rlb_mie_fd_keeps_it(orc):
     assert res[0][0] <= 1.0 and res[0][1]
     assert res[1][0] > 1.0
     assert res[0][2] < res[1][2]
+
+
+def test_phase_volume_closed_forms(orc):
+    """h^d sum (1 + phi)/2: 0 for phi = -1, h^d N for phi = +1, half for phi = 0."""
+    for shape, h in (((10,), 0.1), ((4, 5), 0.25), ((3, 4, 5), 0.5)):
+        d = len(shape)
+        N = int(np.prod(shape))
+        assert orc.phase_volume(-np.ones(shape), h) == 0.0
+        assert orc.phase_volume(np.ones(shape), h) == pytest.approx(h ** d * N, rel=1e-15)
+        assert orc.phase_volume(np.zeros(shape), h) == pytest.approx(0.5 * h ** d * N, rel=1e-15)
+
+
+def test_mean_curvature_circle_radius(orc):
+    """Sec. IV.B.2: a circle of radius 0.7 on (-1, 1)^2 (Neumann, dx = 1/64, dt = 1/100,
+    eps = 5 dx tanh(0.9)/sqrt 2) shrinks as R(t) = sqrt(R0^2 - 2 eps^2 t); the radius from
+    the phase area follows the law's decrease to 1 % over t = 0..10."""
+    h, dt, R0 = 1 / 64, 0.01, 0.7
+    eps = 5 * h * math.tanh(0.9) / math.sqrt(2)
+    x = -1 + h * np.arange(round(2 / h) + 1)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    phi = np.tanh((R0 - np.sqrt(X ** 2 + Y ** 2)) / (math.sqrt(2) * eps))
+    R = lambda p: math.sqrt(orc.phase_volume(p, h) / math.pi)
+    r0 = R(phi)
+    phi = orc.run_fd(phi, eps, dt, h, 1, 1000)
+    drop = r0 - R(phi)
+    exact_drop = R0 - math.sqrt(R0 ** 2 - 2 * eps ** 2 * 10.0)
+    assert drop == pytest.approx(exact_drop, rel=0.01)
