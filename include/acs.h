@@ -74,13 +74,16 @@ enum {
     ACS_E_UNSUPPORTED = -7         /* kernel variant not available for this problem */
 };
 
-/* Kernel variants (acs_set_kernel).  All variants compute the same per-point
- * arithmetic in the same order, so they give bit-identical states. */
+/* Kernel variants (acs_set_kernel).  The finite-difference variants (1..3) compute
+ * the same per-point arithmetic in the same order, so they give bit-identical
+ * states.  ACS_KERNEL_LB runs the collide-and-stream form the scheme is derived
+ * from (Sec. II): equal to Eq. (IE-FD) up to rounding. */
 enum {
     ACS_KERNEL_AUTO = 0,     /* autotuned choice, cached per problem class */
     ACS_KERNEL_NAIVE = 1,    /* one thread per unknown, neighbours via the cache hierarchy */
     ACS_KERNEL_TILED = 2,    /* shared-memory tiles (TMA-staged for d >= 2) with a one-cell halo */
-    ACS_KERNEL_TEMPORAL = 3  /* several fused steps per pass through HBM (temporal blocking) */
+    ACS_KERNEL_TEMPORAL = 3, /* several fused steps per pass through HBM (temporal blocking) */
+    ACS_KERNEL_LB = 4        /* 2d+1 stored populations: collide, then stream + solve (acs_lb_bind) */
 };
 
 /* Schemes (acs_set_scheme).  RLB-MIE-FD is the paper's scheme (Eq. IE-FD); FEX-FD
@@ -145,6 +148,24 @@ ACS_API int acs_set_scheme(acs_ctx* ctx, int scheme);
 ACS_API int acs_set_kernel(acs_ctx* ctx, int kernel, int depth);
 /* The variant acs_step() uses (after autotuning, for ACS_KERNEL_AUTO). */
 ACS_API int acs_get_kernel(const acs_ctx* ctx, int* kernel, int* depth);
+
+/*
+ * Collide-and-stream (population) form, Sec. II: Eqs. (fieq-Fi), (fneq), (RLB),
+ * (pine).  A DdQ(2d+1) lattice keeps 2d+1 populations per node; one step collides
+ * every node into g_k = w_k phi - ((1 - s) w_1 / s)(phi(y + c_k dt) - phi(y))
+ * (g_0 = w_0 phi, s = w_1 / lambda), streams them, and solves the cubic of
+ * Remark 1 for the summed value.  It is the form Eq. (IE-FD) removes; it is kept
+ * to measure what the macroscopic form saves in memory and traffic.
+ *
+ * acs_lb_bytes  size of the population buffer: (2 dims + 1) * prod(n) elements.
+ * acs_lb_bind   d_pop: that many bytes, 16-byte aligned, caller-owned, valid while
+ *               ACS_KERNEL_LB is selected; omega1: the weight w_1 in (0, 1/(2d)],
+ *               or 0 for the paper's choice (1/3, 1/5, 1/6 for d = 1, 2, 3).
+ *               Then acs_set_kernel(ctx, ACS_KERNEL_LB, 1) selects the form
+ *               (ACS_E_STATE before acs_lb_bind; ACS_E_UNSUPPORTED with FEX-FD).
+ */
+ACS_API size_t acs_lb_bytes(const acs_ctx* ctx);
+ACS_API int acs_lb_bind(acs_ctx* ctx, void* d_pop, size_t bytes, double omega1);
 
 /* Number of tile shapes (rows per thread x ring depth) the tiled kernels offer. */
 ACS_API int acs_num_variants(void);
@@ -283,16 +304,36 @@ ACS_API void acs_destroy(acs_ctx* ctx);
 
 /*
  * Batched stepping: `count` independent 2D problems of sides n[i] x n[i], each
- * with its own eps, dt, h and boundary, advanced together in one persistent
- * launch per call (recorded into a CUDA graph).  The states are packed one after
- * the other in one device buffer; acs_batch_offsets() gives each instance's first
- * element.  Per-instance arithmetic is identical to acs_step() on that instance
- * alone, so each instance's state is bit-identical to its standalone run.
+ * with its own eps, dt, h and boundary (Sec. I, Eq. IE-FD), advanced together in
+ * one persistent launch per call (recorded into a CUDA graph).  The paper has no
+ * batched form; this is many copies of the 2D step.
+ *
+ * Layout: the states are packed one after the other in one device buffer of
+ * acs_batch_numel() elements.  Instance i starts at element offsets[i]
+ * (acs_batch_offsets) and its rows are row_strides[i] elements apart
+ * (acs_batch_row_strides: n[i] rounded up to a multiple of 16 bytes); row y,
+ * column x of instance i is element offsets[i] + y * row_strides[i] + x.  The
+ * padding after each row is never read into a result nor written.
+ *
+ * Per-instance arithmetic is identical to acs_step() on that instance alone, so
+ * each instance's state is bit-identical to its standalone run.
+ *
+ * acs_batch_create  validates every instance (as acs_create) and plans the work;
+ *                   returns the strongest ACS_WARN_* over the instances, or an error
+ *                   (ACS_E_INVAL) with *out untouched.  The caller owns *out
+ *                   (acs_batch_destroy).
+ * acs_batch_bind    d_phi: the packed states (16-byte aligned, caller-owned, stays
+ *                   valid while bound); d_work: acs_batch_work_bytes() bytes, 256-byte
+ *                   aligned, caller-owned; stream: where every call is enqueued.
+ *                   ACS_E_UNSUPPORTED if the TMA descriptors cannot be encoded.
+ * acs_batch_step    advances every instance n_steps (asynchronous on the stream).
  */
 ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, const double* dt,
                              const double* h, const int* bc, int dtype, acs_batch** out);
 ACS_API size_t acs_batch_numel(const acs_batch* b);
 ACS_API int acs_batch_offsets(const acs_batch* b, int64_t* offsets);
+/* Row stride (elements) of every instance into `count` int64 values. */
+ACS_API int acs_batch_row_strides(const acs_batch* b, int64_t* row_strides);
 ACS_API size_t acs_batch_work_bytes(const acs_batch* b);
 ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_bytes, void* stream);
 ACS_API int acs_batch_step(acs_batch* b, int64_t n_steps);

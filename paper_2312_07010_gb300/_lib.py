@@ -17,7 +17,7 @@ ACS_OK = 0
 ACS_WARN_MP_CONDITION, ACS_WARN_ENERGY_CONDITION = 1, 2
 ACS_E_INVAL, ACS_E_CUDA, ACS_E_NOMEM, ACS_E_TIMEOUT = -1, -2, -3, -4
 ACS_E_NONFINITE, ACS_E_STATE, ACS_E_UNSUPPORTED = -5, -6, -7
-ACS_KERNEL_AUTO, ACS_KERNEL_NAIVE, ACS_KERNEL_TILED, ACS_KERNEL_TEMPORAL = 0, 1, 2, 3
+ACS_KERNEL_AUTO, ACS_KERNEL_NAIVE, ACS_KERNEL_TILED, ACS_KERNEL_TEMPORAL, ACS_KERNEL_LB = 0, 1, 2, 3, 4
 ACS_SCHEME_RLB_MIE_FD, ACS_SCHEME_FEX_FD = 0, 1
 
 # every function include/acs.h declares: name -> (restype, argtypes)
@@ -58,10 +58,13 @@ SIGNATURES = {
     "acs_strerror": (_c.c_char_p, [_c.c_int]),
     "acs_version": (_c.c_char_p, []),
     "acs_destroy": (None, [_vp]),
+    "acs_lb_bytes": (_c.c_size_t, [_vp]),
+    "acs_lb_bind": (_c.c_int, [_vp, _vp, _c.c_size_t, _c.c_double]),
     "acs_batch_create": (_c.c_int, [_c.c_int, _i64p, _dp, _dp, _dp, _c.POINTER(_c.c_int), _c.c_int,
                                     _c.POINTER(_vp)]),
     "acs_batch_numel": (_c.c_size_t, [_vp]),
     "acs_batch_offsets": (_c.c_int, [_vp, _i64p]),
+    "acs_batch_row_strides": (_c.c_int, [_vp, _i64p]),
     "acs_batch_work_bytes": (_c.c_size_t, [_vp]),
     "acs_batch_bind": (_c.c_int, [_vp, _vp, _vp, _c.c_size_t, _vp]),
     "acs_batch_step": (_c.c_int, [_vp, _i64]),

@@ -1,7 +1,8 @@
 """Batched stepping (acs_batch_*): many independent 2D problems in one persistent launch.
 
 ``Batch`` packs the instances' states into one device buffer (torch) and forwards to the
-C ABI; instance i lives at ``phi[offsets[i] : offsets[i] + n_i * n_i]`` (row-major).
+C ABI; row y, column x of instance i is ``phi[offsets[i] + y * ld[i] + x]`` with the row
+stride ``ld[i]`` (n_i rounded up to 16 bytes) from acs_batch_row_strides.
 """
 from __future__ import annotations
 
@@ -34,6 +35,9 @@ class Batch:
         offs = (ctypes.c_int64 * self.count)()
         check(self.L.acs_batch_offsets(self.b, offs), "acs_batch_offsets")
         self.offsets = [int(v) for v in offs]
+        lds = (ctypes.c_int64 * self.count)()
+        check(self.L.acs_batch_row_strides(self.b, lds), "acs_batch_row_strides")
+        self.ld = [int(v) for v in lds]
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self.phi = torch.zeros(self.numel, dtype=self.tdtype, device="cuda")
         wb = int(self.L.acs_batch_work_bytes(self.b))
@@ -42,21 +46,31 @@ class Batch:
                                     wb, ctypes.c_void_p(self.stream.cuda_stream)), "acs_batch_bind")
 
     def view(self, i: int) -> torch.Tensor:
-        o = self.offsets[i]
-        return self.phi[o:o + self.n[i] * self.n[i]].view(self.n[i], self.n[i])
+        """Instance i as an n_i x n_i strided view of the packed device buffer."""
+        o, n, ld = self.offsets[i], self.n[i], self.ld[i]
+        return self.phi[o:o + n * ld].view(n, ld)[:, :n]
 
-    def set_states(self, states: List[np.ndarray]) -> None:
+    def pack(self, states: List[np.ndarray]) -> torch.Tensor:
+        """Host (CPU) tensor of the packed layout holding `states` (zero padding)."""
         host = torch.zeros(self.numel, dtype=self.tdtype)
         for i, s in enumerate(states):
-            o = self.offsets[i]
-            host[o:o + self.n[i] * self.n[i]] = torch.from_numpy(np.ascontiguousarray(s, dtype=self.ndtype).ravel())
-        self.phi.copy_(host.to("cuda"))
+            o, n, ld = self.offsets[i], self.n[i], self.ld[i]
+            a = torch.from_numpy(np.ascontiguousarray(s, dtype=self.ndtype).reshape(n, n))
+            host[o:o + n * ld].view(n, ld)[:, :n] = a
+        return host
+
+    def unpack(self, host: np.ndarray) -> List[np.ndarray]:
+        """The instances' states (copies) out of a packed host array."""
+        return [host[o:o + n * ld].reshape(n, ld)[:, :n].copy()
+                for o, n, ld in zip(self.offsets, self.n, self.ld)]
+
+    def set_states(self, states: List[np.ndarray]) -> None:
+        self.phi.copy_(self.pack(states).to("cuda"))
         torch.cuda.synchronize()
 
     def states(self) -> List[np.ndarray]:
         torch.cuda.synchronize()
-        host = self.phi.cpu().numpy()
-        return [host[o:o + n * n].reshape(n, n).copy() for o, n in zip(self.offsets, self.n)]
+        return self.unpack(self.phi.cpu().numpy())
 
     def step(self, n: int) -> None:
         check(self.L.acs_batch_step(self.b, int(n)), "acs_batch_step")

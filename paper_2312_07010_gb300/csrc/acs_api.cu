@@ -46,6 +46,35 @@ static void pick_newton(double t, double rb, double tol, int* newton, double* ym
     *ymax = lo;
 }
 
+// Corrections after the rational seed xi / (b + a xi^2) so that the root is accurate to
+// tol for every |xi| <= 1.001, or 0 if kmax do not suffice.  The seed's relative error
+// e0 and the contraction K = max 3 a theta^2 / (3 a theta^2 + b) of the relative error
+// (e -> K e^2 for exact Newton) are sampled on a fine grid; the approximate
+// reciprocal adds eta e per correction.
+static int pick_rational(double a, double b, double tol, int kmax) {
+    const int N = 4096;
+    double e0 = 0.0, K = 0.0;
+    for (int i = 1; i <= N; ++i) {
+        const double xi = 1.001 * i / N;
+        const double seed = xi / (b + a * xi * xi);
+        double th = seed;  // an upper bound: Newton descends monotonically to the root
+        for (int it = 0; it < 200; ++it) {
+            const double nt = th - (a * th * th * th + b * th - xi) / (3.0 * a * th * th + b);
+            if (!(nt < th)) break;
+            th = nt;
+        }
+        e0 = std::max(e0, std::fabs(seed / th - 1.0));
+        K = std::max(K, 3.0 * a * th * th / (3.0 * a * th * th + b));
+    }
+    const double eta = 2.5e-7;
+    double e = e0 * 1.05 + eta;  // sampling margin; the seed's own approximate reciprocal
+    for (int k = 1; k <= kmax; ++k) {
+        e = K * e * e + eta * e;
+        if (e <= tol) return k;
+    }
+    return 0;
+}
+
 // Lagrange-inversion coefficients C_k = binom(3k, k) / (2k + 1).
 static const double kLagrangeC[11] = {1, 1, 3, 12, 55, 273, 1428, 7752, 43263, 246675, 1430715};
 
@@ -99,6 +128,14 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
         double ymax;
         pick_newton(t, rb, tol, &c.newton, &ymax);
         c.ymax = (T)ymax;
+        c.seed = 0;
+        if (c.solve == kSolveNewton && cubic_bound(yneed, c.newton) > tol) {
+            // the three-term seed does not cover |xi| <= 1.001: the rational seed does
+            const int k = pick_rational(a, b, tol, NewtonMax<T>::value);
+            c.seed = 1;
+            c.newton = k;
+            c.xi2max = (T)(k > 0 ? 1.001 * 1.001 : -1.0);
+        }
     }
     const double ulp1 = sizeof(T) == 4 ? std::ldexp(1.0, -23) : std::ldexp(1.0, -52);
     c.clamp_hi = (T)(1.0 + 16.0 * ulp1);
@@ -109,6 +146,8 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
         double f2 = (double)c.xi2max;
         if (c.clamp) f2 = std::min(f2, (1.0 + 8.0 * ulp1) * (1.0 + 8.0 * ulp1));
         c.fast2max = (T)f2;
+    } else if (c.solve == kSolveNewton) {
+        c.fast2max = (T)(c.clamp ? (1.0 + 8.0 * ulp1) * (1.0 + 8.0 * ulp1) : 1e30);
     }
     return c;
 }
@@ -167,6 +206,9 @@ struct acs_ctx {
     int variant;       // tile shape of the tiled kernels
     bool tuned;        // the autotuner has run (or the cache answered) for this context
     int64_t steps_done;
+    void* pop;         // population buffer of ACS_KERNEL_LB (caller-owned), or null
+    size_t pop_bytes;
+    double omega1;     // lattice weight w_1 of ACS_KERNEL_LB
     std::vector<GraphEntry> graphs;
     // adjoint recording
     GradState grad;
@@ -204,6 +246,8 @@ static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaS
     if (c->dtype == ACS_F32) {
         const float* s = (const float*)src;
         float* d = (float*)dst;
+        if (c->kernel == ACS_KERNEL_LB)
+            return launch_step_lb<float>(c->dims, c->bc, s, (float*)c->pop, d, c->g, c->omega1, c->lam, c->cf, st);
         if (c->kernel == ACS_KERNEL_TEMPORAL)
             return launch_step_temporal<float>(c->dims, c->bc, k, s, d, c->g, c->cf, c->err, st);
         if (c->kernel == ACS_KERNEL_TILED)
@@ -212,6 +256,8 @@ static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaS
     }
     const double* s = (const double*)src;
     double* d = (double*)dst;
+    if (c->kernel == ACS_KERNEL_LB)
+        return launch_step_lb<double>(c->dims, c->bc, s, (double*)c->pop, d, c->g, c->omega1, c->lam, c->cd, st);
     if (c->kernel == ACS_KERNEL_TEMPORAL)
         return launch_step_temporal<double>(c->dims, c->bc, k, s, d, c->g, c->cd, c->err, st);
     if (c->kernel == ACS_KERNEL_TILED)
@@ -336,9 +382,9 @@ static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, c
 namespace acs {
 cudaError_t ctx_enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st) { return enqueue_steps(c, n, st); }
 cudaError_t ctx_launch_one(acs_ctx* c, const void* src, void* dst, cudaStream_t st) {
-    // one step; every variant gives identical bits, so use the context's tiled kernel
-    // when it has one
-    if (c->kernel == ACS_KERNEL_TILED) return launch_k(c, 1, src, dst, st);
+    // one step; every FD variant gives identical bits, so use the context's tiled
+    // kernel when it has one; the population form recomputes with itself
+    if (c->kernel == ACS_KERNEL_TILED || c->kernel == ACS_KERNEL_LB) return launch_k(c, 1, src, dst, st);
     if (c->dtype == ACS_F32)
         return launch_step_naive<float>(c->dims, c->bc, (const float*)src, (float*)dst, c->g, c->cf, st);
     return launch_step_naive<double>(c->dims, c->bc, (const double*)src, (double*)dst, c->g, c->cd, st);
@@ -424,6 +470,9 @@ ACS_API int acs_create(int dims, const int64_t n[3], double eps, double dt, doub
     c->zchunk = 0;
     c->variant = 0;
     c->tuned = false;
+    c->pop = nullptr;
+    c->pop_bytes = 0;
+    c->omega1 = 0.0;
     c->grad = GradState();
     resolve_auto_kernel(c->dims, c->dtype, c->bc, c->g, &c->kernel, &c->depth);
     *out = c;
@@ -459,6 +508,7 @@ ACS_API int acs_bind(acs_ctx* c, void* d_phi, void* d_work, size_t work_bytes, v
 
 ACS_API int acs_set_scheme(acs_ctx* c, int scheme) {
     if (!c || (scheme != ACS_SCHEME_RLB_MIE_FD && scheme != ACS_SCHEME_FEX_FD)) return ACS_E_INVAL;
+    if (c->kernel == ACS_KERNEL_LB && scheme != ACS_SCHEME_RLB_MIE_FD) return ACS_E_UNSUPPORTED;
     c->scheme = scheme;
     refresh_coef(c);
     drop_graphs(c);
@@ -486,6 +536,14 @@ ACS_API int acs_set_kernel(acs_ctx* c, int kernel, int depth) {
         drop_graphs(c);
         return ACS_OK;
     }
+    if (kernel == ACS_KERNEL_LB) {
+        if (!c->pop) return ACS_E_STATE;
+        if (c->scheme != ACS_SCHEME_RLB_MIE_FD) return ACS_E_UNSUPPORTED;
+        c->kernel_req = c->kernel = kernel;
+        c->depth = 1;
+        drop_graphs(c);
+        return ACS_OK;
+    }
     if (kernel == ACS_KERNEL_TEMPORAL) {
         if (depth < 1 || depth > 8) return ACS_E_INVAL;
         if (!temporal_supported(c->dims, c->dtype, depth, c->g)) return ACS_E_UNSUPPORTED;
@@ -501,6 +559,23 @@ ACS_API int acs_get_kernel(const acs_ctx* c, int* kernel, int* depth) {
     if (!c) return ACS_E_INVAL;
     if (kernel) *kernel = c->kernel;
     if (depth) *depth = c->depth;
+    return ACS_OK;
+}
+
+ACS_API size_t acs_lb_bytes(const acs_ctx* c) {
+    return c ? (size_t)(2 * c->dims + 1) * state_bytes(c) : 0;
+}
+
+ACS_API int acs_lb_bind(acs_ctx* c, void* d_pop, size_t bytes, double omega1) {
+    if (!c || !d_pop || ((uintptr_t)d_pop % 16)) return ACS_E_INVAL;
+    if (!std::isfinite(omega1) || omega1 > 1.0 / (2.0 * c->dims) * (1.0 + 1e-15)) return ACS_E_INVAL;
+    if (bytes < acs_lb_bytes(c)) return ACS_E_NOMEM;
+    // the paper's weights: w_1 = 1/3, 1/5, 1/6 for d = 1, 2, 3 (Sec. IV)
+    static const double kDefaultW1[4] = {0.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 6.0};
+    c->omega1 = omega1 > 0.0 ? omega1 : kDefaultW1[c->dims];
+    c->pop = d_pop;
+    c->pop_bytes = bytes;
+    drop_graphs(c);
     return ACS_OK;
 }
 

@@ -15,12 +15,14 @@ namespace acs {
 // Cubic-solve modes (a template parameter of every stepping kernel; the host picks
 // one per context, so all variants of that context round identically).
 enum Solve : int {
-    kSolveNewton = 0,  // three-term series seed + `newton` Newton corrections
+    kSolveNewton = 0,  // a seed (three-term series or rational) + `newton` Newton corrections
     kSolveSeries = 1,  // SeriesTerms<T> terms of the Lagrange series, no division
     kSolveFex = 2      // FEX-FD scheme of Remark 2: no cubic at all
 };
 template <typename T>
 struct SeriesTerms { static constexpr int value = sizeof(T) == 4 ? 5 : 9; };
+template <typename T>
+struct NewtonMax { static constexpr int value = sizeof(T) == 4 ? 4 : 6; };
 
 // Coefficients of one step in the state's precision T.
 //   lam = eps^2 dt / h^2 (Eq. IE-FD-vector-form), a = dt/2, b = 1 - a.
@@ -42,7 +44,8 @@ struct Coef {
     T fast2max;   // several-points fast path (tiled kernels): xi^2 bound, see roots()
     T rb, t;      // kSolveNewton: 1/b, a/b
     T ymax;       // kSolveNewton applies while y = t (xi/b)^2 <= ymax
-    int newton;   // kSolveNewton: corrections after the seed (1..3)
+    int newton;   // kSolveNewton: corrections after the seed (1..6)
+    int seed;     // kSolveNewton: 0 = three-term series in y (y <= ymax), 1 = xi / (b + a xi^2) (xi^2 <= xi2max)
     T clamp_hi;   // 1 + 16 ulp: overshoots up to this are rounding and go back to +-1
     int clamp;    // 1: apply that rounding guard (set only when Theorem 2's condition holds)
     int solve;    // the Solve mode this context uses
@@ -87,6 +90,36 @@ __device__ __noinline__ T cubic_robust(T xi, T a, T b) {
     return xi < T(0) ? -th : th;
 }
 
+// Seeds of the Newton solve.  seed3: the Lagrange series in y = (a/b) x^2, x = xi/b,
+// cut after three terms.  rational: xi / (b + a xi^2), exact at xi = 0 and xi = +-1
+// (a + b = 1) and an upper bound of |theta| in between (|theta| >= |xi| there), so
+// the corrections descend monotonically.
+template <typename T>
+__device__ __forceinline__ T newton_seed3(T x, T y) {
+    const T u = -y;
+    return x * dfma(u, dfma(T(3), u, T(1)), T(1));
+}
+template <typename T>
+__device__ __forceinline__ T newton_seed_rational(T xi, T x2, const Coef<T>& c) {
+    return xi * arcp(dfma(c.a, x2, c.b));
+}
+// c.newton Newton corrections theta -= p(theta) / p'(theta) with an approximate
+// reciprocal (the host counted them from an error bound that includes its error);
+// at most NewtonMax<T> of them.
+template <typename T>
+__device__ __forceinline__ T newton_fix(T th, T xi, const Coef<T>& c) {
+#pragma unroll
+    for (int k = 0; k < NewtonMax<T>::value; ++k) {
+        if (k < c.newton) {
+            const T th2 = th * th;
+            const T p = dfma(dfma(c.a, th2, c.b), th, -xi);
+            const T dp = dfma(c.three_a, th2, c.b);
+            th = dfma(-p, arcp(dp), th);
+        }
+    }
+    return th;
+}
+
 // Root of theta + (dt/2) f(theta) = xi (Remark 1), i.e. a theta^3 + b theta = xi.
 // The host picks the mode and its limits from a-priori error bounds so that the
 // fast paths are accurate to the last bit of T for |xi| <= 1.001 (Theorem 2's
@@ -106,23 +139,19 @@ __device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
             th = cubic_robust(xi, c.a, c.b);
         }
     } else {
-        const T x = xi * c.rb;
-        const T y = (c.t * x) * x;
-        if (y <= c.ymax) {
-            const T u = -y;
-            th = x * dfma(u, dfma(T(3), u, T(1)), T(1));
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (k < c.newton) {
-                    const T th2 = th * th;
-                    const T p = dfma(dfma(c.a, th2, c.b), th, -xi);
-                    const T dp = dfma(c.three_a, th2, c.b);
-                    th = dfma(-p, arcp(dp), th);
-                }
-            }
+        bool ok;
+        if (c.seed == 0) {
+            const T x = xi * c.rb;
+            const T y = (c.t * x) * x;
+            ok = y <= c.ymax;
+            th = newton_seed3(x, y);
         } else {
-            th = cubic_robust(xi, c.a, c.b);
+            const T x2 = xi * xi;
+            ok = x2 <= c.xi2max;
+            th = newton_seed_rational(xi, x2, c);
         }
+        if (ok) th = newton_fix(th, xi, c);
+        else th = cubic_robust(xi, c.a, c.b);
     }
     if (c.clamp) {
         const T ath = th < T(0) ? -th : th;

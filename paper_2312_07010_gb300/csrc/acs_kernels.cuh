@@ -30,6 +30,12 @@ template <typename T>
 cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* dst, const Geo& g,
                                  const Coef<T>& c, int* err, cudaStream_t st);
 bool tiled_supported(int dims, int dtype, const Geo& g);
+
+// Collide-and-stream (population) form of the step: pop holds (2 dims + 1) * total
+// values; omega1 is the lattice weight w_1 and lam = eps^2 dt / h^2 (s = w_1 / lam).
+template <typename T>
+cudaError_t launch_step_lb(int dims, int bc, const T* src, T* pop, T* dst, const Geo& g, double omega1,
+                           double lam, const Coef<T>& cf, cudaStream_t st);
 bool temporal_supported(int dims, int dtype, int depth, const Geo& g);
 
 // E_h and max |phi| with the TMA-streamed pipeline (3D, rows a multiple of 16 bytes);

@@ -131,24 +131,35 @@ __global__ void __launch_bounds__(256) k_adjoint2d(const T* __restrict__ phin, c
     using TT = Tile2<T>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T* P = reinterpret_cast<T*>(sm_raw);
-    T* Q = P + TT::N;
-    T* M = Q + TT::N;
     const int ny = (int)g.ny, nx = (int)g.nx;
     const int ntiles = ntx * nty;
     const int t0 = blockIdx.x * per_cta, t1 = min(t0 + per_cta, ntiles);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     CSum ge{0.0, 0.0};
-    for (int t = t0; t < t1; ++t) {
+    // two sets of (phi^n, phi^{n+1}, adj^{n+1}) tiles: the next tile is staged while
+    // the current one is processed
+    auto stage = [&](int t, int set) {
         const int x0 = (t / nty) * TT::TX, y0 = (t % nty) * TT::TY;
-        stage_tile<T>(P, phin, ny, nx, BC, x0, y0);
-        stage_tile<T>(Q, phin1, ny, nx, BC, x0, y0);
-        stage_tile<T>(M, adj1, ny, nx, BC, x0, y0);
+        T* base = P + set * 3 * TT::N;
+        stage_tile<T>(base, phin, ny, nx, BC, x0, y0);
+        stage_tile<T>(base + TT::N, phin1, ny, nx, BC, x0, y0);
+        stage_tile<T>(base + 2 * TT::N, adj1, ny, nx, BC, x0, y0);
+    };
+    if (t0 < t1) stage(t0, 0);
+    cp_async_commit();
+    for (int t = t0; t < t1; ++t) {
+        const int set = (t - t0) & 1;
+        if (t + 1 < t1) stage(t + 1, set ^ 1);
         cp_async_commit();
-        cp_async_wait<0>();
+        cp_async_wait<1>();
         __syncthreads();
+        const int x0 = (t / nty) * TT::TX, y0 = (t % nty) * TT::TY;
+        T* Pc = P + set * 3 * TT::N;
+        T* Qc = Pc + TT::N;
+        T* Mc = Qc + TT::N;
         for (int i = threadIdx.x; i < TT::N; i += TT::THREADS) {
-            const T q = Q[i];
-            M[i] = M[i] / dfma(cf.three_a, q * q, cf.b);
+            const T q = Qc[i];
+            Mc[i] = Mc[i] / dfma(cf.three_a, q * q, cf.b);
         }
         __syncthreads();
         T tile_sum = T(0);
@@ -161,9 +172,9 @@ __global__ void __launch_bounds__(256) k_adjoint2d(const T* __restrict__ phin, c
                 const int cx = lane + 32 * k;  // tile column (staged column VX + cx)
                 const int gx = x0 + cx;
                 const int i = (r + 1) * TT::BW + TT::VX + cx;
-                const T mu = M[i], p = P[i];
-                const T smu = nsum(M[i - TT::BW], M[i + TT::BW], M[i - 1], M[i + 1]);
-                const T sphi = nsum(P[i - TT::BW], P[i + TT::BW], P[i - 1], P[i + 1]);
+                const T mu = Mc[i], p = Pc[i];
+                const T smu = nsum(Mc[i - TT::BW], Mc[i + TT::BW], Mc[i - 1], Mc[i + 1]);
+                const T sphi = nsum(Pc[i - TT::BW], Pc[i + TT::BW], Pc[i - 1], Pc[i + 1]);
                 if (gy < ny && gx < nx) {
                     adj0[(int64_t)gy * nx + gx] = dfma(cf.lam, smu, mu * dfma(-cf.three_a, p * p, cf.c0));
                     tile_sum = dfma(mu, sphi - T(4) * p, tile_sum);
@@ -189,7 +200,7 @@ static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin
         const int64_t ntiles = (int64_t)ntx * nty;
         const int per = (int)std::max<int64_t>(1, (ntiles + kMaxRedBlocks - 1) / kMaxRedBlocks);
         const int grid = (int)((ntiles + per - 1) / per);
-        const size_t smem = 3 * TT::N * sizeof(T);
+        const size_t smem = 6 * TT::N * sizeof(T);
         cudaError_t e = cudaSuccess;
         auto kern = bc == 0 ? k_adjoint2d<T, 0> : (bc == 1 ? k_adjoint2d<T, 1> : k_adjoint2d<T, 2>);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,12 +1,18 @@
 // batch.cu -- many independent 2D problems advanced together in one persistent,
 // cooperative launch per acs_batch_step() call (recorded once into a CUDA graph).
 //
-// Every instance is cut into 128 x 16 tiles; the tiles of all instances form one
-// list, and each CTA owns a contiguous run of it (so its tiles mostly belong to one
-// instance).  Per time step a CTA stages and updates its tiles exactly as the
-// single-problem 2D kernel does (same ghost rules, same per-point arithmetic, same
-// coefficients), then all CTAs meet at a software grid barrier before the next
-// step.  Each instance is therefore bit-identical to its standalone run.
+// Layout: the states are packed one after the other; the rows of instance i are
+// ld_i = n_i rounded up to a 16-byte multiple apart (acs_batch_row_strides), so
+// every instance has its own TMA tensor maps, one per ping-pong buffer.
+//
+// Work: every instance is cut into blocks of TX columns x 16 rows (TX = 128 FP32,
+// 64 FP64), listed instance after instance, down each column strip.  Each CTA owns
+// a contiguous run of that list and streams it through one ring of TMA-loaded boxes
+// exactly as the single-problem 2D kernel streams its column (same halo boxes, same
+// ghost rules, same per-point arithmetic and coefficients), so each instance is
+// bit-identical to its standalone run.  The ring runs on across block and instance
+// boundaries; at the end of its run a CTA meets the others at a software grid
+// barrier before the next step's loads are issued.
 //
 // The barrier spins with a one-second bound (%globaltimer); a CTA that gives up
 // records ACS_E_TIMEOUT and raises an abort flag that releases every other waiter,
@@ -17,34 +23,68 @@
 #include <vector>
 
 #include "acs_host.h"
-#include "tile2d.cuh"
+#include "stream_tile.cuh"
 #include "tma.cuh"
 
 namespace acs {
 
 template <typename T>
 struct DevInst {
-    int64_t off;    // first element of the instance in the packed state
-    int nx, ny;     // sides (x fastest)
+    int64_t off;  // first element of the instance in the packed state
+    int n;        // side (x fastest)
+    int ld;       // row stride in elements (a 16-byte multiple)
     int bc;
-    int nty;        // tiles along y
-    int tile0;      // index of its first tile in the global tile list
-    int ntiles;
+    int pad;
     Coef<T> c;
 };
 
+// One block of one instance.  colx / rowy: where a periodic instance's wrapped
+// column / row for this block is fetched from when the main box does not hold it
+// (the TMA x coordinate of a VX-wide column box, the y of a one-row box), else -1.
+struct BlockRef {
+    int inst, x0, y0, colx, rowy, pad0, pad1, pad2;
+};
+
+// Tile geometry of the batched kernel: 2 rows per thread, 6 ring slots; blocks are
+// handed out in chunks of kChunk consecutive blocks (one tensor-map set per instance:
+// main box, column box, row box, for each of the two state buffers).
+template <typename T>
+using BatchTile = Tile3<T, 2, 6>;
+constexpr int kChunk = 4;
+constexpr int kMapsPerInst = 6;
+constexpr int kFenceWords = 64;  // instances whose maps a CTA remembers as acquired
+
+template <typename T>
+struct BatchSmem {
+    using TT = BatchTile<T>;
+    static constexpr uint32_t COL_BYTES = TT::VX * TT::BH * sizeof(T);  // VX x BH column box
+    static constexpr uint32_t ROW_BYTES = TT::BW * sizeof(T);           // BW x 1 row box
+    static constexpr uint32_t COL_STRIDE = (COL_BYTES + 127u) / 128u * 128u;
+    static constexpr uint32_t ROW_STRIDE = (ROW_BYTES + 127u) / 128u * 128u;
+    static constexpr uint32_t OFF_RING = TT::BAR_BYTES;
+    static constexpr uint32_t OFF_COL = OFF_RING + TT::S * TT::SLOT_STRIDE;
+    static constexpr uint32_t OFF_ROW = OFF_COL + TT::S * COL_STRIDE;
+    static constexpr uint32_t OFF_META = OFF_ROW + TT::S * ROW_STRIDE;
+    static constexpr size_t BYTES = 128 + OFF_META + TT::S * sizeof(BlockRef);
+};
+
 struct BarrierState {
-    unsigned count;  // arrivals in the current phase
-    unsigned gen;    // phase counter
-    int abort;       // set by a waiter that gave up: everyone leaves
-    int inject;      // testing aid: 1 = the last CTA skips one arrival
+    unsigned count;   // arrivals in the current phase
+    unsigned gen;     // phase counter
+    int abort;        // set by a waiter that gave up: everyone leaves
+    int inject;       // testing aid: 1 = the last CTA skips one arrival
+    unsigned ctr[4];  // chunk tickets of step s in ctr[s & 3] (zeroed before each launch)
 };
 
 // Returns false (and the CTA must leave) if the barrier was aborted or timed out.
-__device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned nblocks, int* err, bool skip_arrival) {
+// The last arrival after step `step` zeroes the ticket counter of step + 2 (last used
+// at step - 2, two barriers ago).  Thread (0, 0), which also issues the TMA loads,
+// orders the other CTAs' stores before its next loads through the async proxy.
+__device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned nblocks, int step, int* err,
+                                             bool skip_arrival) {
     __shared__ int s_ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
         int ok = 1;
         volatile unsigned* vgen = &bs->gen;
         volatile int* vabort = &bs->abort;
@@ -54,6 +94,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned nblocks,
             const unsigned arrived = atomicAdd(&bs->count, 1u);
             if (arrived == nblocks - 1) {
                 atomicExch(&bs->count, 0u);
+                atomicExch(&bs->ctr[(step + 2) & 3], 0u);
                 __threadfence();
                 atomicAdd(&bs->gen, 1u);
             }
@@ -70,6 +111,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned nblocks,
             }
         }
         __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         s_ok = ok;
     }
     __syncthreads();
@@ -77,70 +119,235 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned nblocks,
     return s_ok != 0;
 }
 
-template <typename T>
-__device__ __forceinline__ void batch_update_tile(const T* buf, T* dst, const DevInst<T>& in, int x0, int y0,
-                                                  const Coef<T>& c) {
-    if (c.solve == kSolveSeries) update_tile<T, kSolveSeries>(buf, dst, in.ny, in.nx, x0, y0, c);
-    else if (c.solve == kSolveFex) update_tile<T, kSolveFex>(buf, dst, in.ny, in.nx, x0, y0, c);
-    else update_tile<T, kSolveNewton>(buf, dst, in.ny, in.nx, x0, y0, c);
+// One block of one instance from its TMA box `cur` (rows y0 - 1 .. y0 + 16, columns
+// x0 - VX .. x0 + TX + VX - 1, zero outside the instance): the body of the
+// single-problem 2D kernel with the boundary taken at run time.  EDGE blocks touch a
+// periodic or Neumann boundary and fix the ghost values there: the first and last
+// rows, the first column, and the last column n - 1 (which need not end a vector:
+// rows are padded).  Periodic wrap values come from the main box when it holds them,
+// else from the column box `colb` (VX x BH) or the row box `rowb` (BW x 1) loaded
+// with the block, so no block reads global memory.
+template <typename T, int SOLVE, bool EDGE>
+__device__ __forceinline__ void batch_block(const T* cur, const T* colb, const T* rowb, T* dst, int n, int bc,
+                                            int64_t sy, const Coef<T>& c, const BlockRef& br) {
+    using TT = BatchTile<T>;
+    constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, RPT = TT::RPT, NP = RPT * VX;
+    const int x0 = br.x0, y0 = br.y0;
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int xl = lx * VX, gx = x0 + xl, r0 = RPT * ly, gy0 = y0 + r0;
+    const bool neu = bc == ACS_BC_NEUMANN;
+    const int lastv = n - 1 - gx;  // vector lane of column n - 1 (if in 0 .. VX - 1)
+    T cz[RPT][VX], below[VX], above[VX], xi[NP];
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) Vec<T>::get(cur + (r0 + rr + 1) * BW + VX + xl, cz[rr]);
+    Vec<T>::get(cur + r0 * BW + VX + xl, below);
+    Vec<T>::get(cur + (r0 + RPT + 1) * BW + VX + xl, above);
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+        const int gyr = gy0 + rr;
+        const int br_row = r0 + rr + 1;  // box row of gyr
+        T ym[VX], yp[VX];
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+            ym[v] = rr == 0 ? below[v] : cz[rr - 1][v];
+            yp[v] = rr == RPT - 1 ? above[v] : cz[rr + 1][v];
+        }
+        T left = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
+        T right = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
+        if (lx == 0) left = cur[br_row * BW + VX - 1];
+        if (lx == 31) right = cur[br_row * BW + VX + TX];
+        T wrapx = T(0);  // periodic: right neighbour of column n - 1
+        if (EDGE && gyr < n) {
+            if (gyr == 0) {
+                if (neu) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) ym[v] = cz[rr][v];
+                } else {
+                    // row n - 1: box row n when it is in the box (n <= TY + 1), else the row box
+                    Vec<T>::get(br.rowy >= 0 ? rowb + VX + xl : cur + n * BW + VX + xl, ym);
+                }
+            }
+            if (gyr == n - 1) {
+                if (neu) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) yp[v] = cz[rr][v];
+                } else {
+                    // row 0: box row 1 of the first block row, else the row box
+                    Vec<T>::get(br.rowy >= 0 ? rowb + VX + xl : cur + BW + VX + xl, yp);
+                }
+            }
+            if (!neu) {
+                // column n - 1 (left of column 0) and column 0 (right of column n - 1)
+                if (gx == 0) left = br.colx >= 0 ? colb[br_row * VX + (n - 1) % VX] : cur[br_row * BW + VX + n - 1];
+                if (lastv >= 0 && lastv < VX) wrapx = br.colx >= 0 ? colb[br_row * VX] : cur[br_row * BW + VX];
+            } else if (gx == 0) {
+                left = cz[rr][0];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+            const T xm = v == 0 ? left : cz[rr][v - 1];
+            T xp = v == VX - 1 ? right : cz[rr][v + 1];
+            if (EDGE && v == lastv) xp = neu ? cz[rr][v] : wrapx;
+            xi[rr * VX + v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
+        }
+    }
+    (void)TY;
+    T out[NP];
+    roots<T, SOLVE, NP>(xi, out, c);
+    T* o = dst + (int64_t)gy0 * sy + gx;
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+        if (gy0 + rr >= n) continue;
+        if (gx + VX <= n) {
+            Vec<T>::put(o + rr * sy, &out[rr * VX]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VX; ++v)
+                if (gx + v < n) o[rr * sy + v] = out[rr * VX + v];
+        }
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst, int count,
-                                                 int total_tiles, int nsteps, BarrierState* bs, int* err) {
-    using TT = Tile2<T>;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* const base = reinterpret_cast<T*>(sm_raw);
-    const int per = (total_tiles + gridDim.x - 1) / gridDim.x;
-    const int t0 = blockIdx.x * per;
-    const int t1 = min(t0 + per, total_tiles);
-    // instance of the first tile (binary search over tile0)
-    int i0 = 0;
-    if (t0 < t1) {
-        int lo = 0, hi = count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (inst[mid].tile0 <= t0) lo = mid; else hi = mid - 1;
-        }
-        i0 = lo;
+__device__ __forceinline__ void batch_block_any(const T* cur, const T* colb, const T* rowb, T* dst, int n, int bc,
+                                                int64_t sy, const Coef<T>& c, const BlockRef& br) {
+    constexpr int TX = BatchTile<T>::TX, TY = BatchTile<T>::TY;
+    const bool edge = bc != ACS_BC_DIRICHLET && (br.x0 == 0 || br.x0 + TX >= n || br.y0 == 0 || br.y0 + TY >= n);
+    ACS_SOLVE_DISPATCH(c.solve, SV, {
+        if (edge) batch_block<T, SV, true>(cur, colb, rowb, dst, n, bc, sy, c, br);
+        else batch_block<T, SV, false>(cur, colb, rowb, dst, n, bc, sy, c, br);
+    });
+}
+
+// Persistent cooperative kernel: nsteps steps of every instance.  Per step, CTAs take
+// chunks of kChunk consecutive blocks from the step's ticket counter (so instances of
+// different cost balance out), stream them through the TMA ring, and meet at the grid
+// barrier.  Thread 0 is the producer: it draws tickets one chunk ahead, issues each
+// block's loads into the next free slot with the block's description in `meta`, and
+// closes the step with an end marker (a slot whose mbarrier completes without data).
+template <typename T>
+__global__ void __launch_bounds__(256, 3) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
+                                                 const CUtensorMap* __restrict__ maps, int count,
+                                                 const BlockRef* __restrict__ blocks, int nblocks, int nsteps,
+                                                 BarrierState* bs, int* err) {
+    using TT = BatchTile<T>;
+    using SM = BatchSmem<T>;
+    constexpr int VX = TT::VX, S = TT::S;
+    constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base);
+    T* ring = reinterpret_cast<T*>(base + SM::OFF_RING);
+    unsigned char* colbase = base + SM::OFF_COL;
+    unsigned char* rowbase = base + SM::OFF_ROW;
+    BlockRef* meta = reinterpret_cast<BlockRef*>(base + SM::OFF_META);
+    __shared__ unsigned fenced[kFenceWords];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const unsigned nchunks = (unsigned)((nblocks + kChunk - 1) / kChunk);
+    if (tid < kFenceWords) fenced[tid] = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
     }
+    __syncthreads();
     const bool injector = bs->inject != 0 && blockIdx.x == gridDim.x - 1;
-    for (int step = 0; step < nsteps; ++step) {
-        const T* src = (step & 1) ? B : A;
-        T* dst = (step & 1) ? A : B;
-        if (t0 < t1) {
-            int ii = i0;
-            auto locate = [&](int t, int& which, int& x0, int& y0) {
-                while (ii + 1 < count && inst[ii + 1].tile0 <= t) ++ii;
-                which = ii;
-                const int lt = t - inst[ii].tile0;
-                x0 = (lt / inst[ii].nty) * TT::TX;
-                y0 = (lt % inst[ii].nty) * TT::TY;
-            };
-            int w, x0, y0;
-            locate(t0, w, x0, y0);
-            stage_tile<T>(base, src + inst[w].off, inst[w].ny, inst[w].nx, inst[w].bc, x0, y0);
-            cp_async_commit();
-            for (int t = t0; t < t1; ++t) {
-                const int cur = (t - t0) & 1;
-                const int cw = w, cx0 = x0, cy0 = y0;
-                if (t + 1 < t1) {
-                    locate(t + 1, w, x0, y0);
-                    stage_tile<T>(base + (cur ^ 1) * TT::N, src + inst[w].off, inst[w].ny, inst[w].nx, inst[w].bc,
-                                  x0, y0);
-                }
-                cp_async_commit();
-                cp_async_wait<1>();
-                __syncthreads();
-                const Coef<T> c = inst[cw].c;
-                batch_update_tile<T>(base + cur * TT::N, dst + inst[cw].off, inst[cw], cx0, cy0, c);
-                __syncthreads();
+
+    // producer state (thread 0 only)
+    int64_t qi = 0;               // next sequence number to fill (slot qi % S, phase (qi / S) & 1)
+    unsigned cur = 0, pf = 0;     // current chunk and the next one (drawn ahead)
+    int j = 0;                    // next block within the current chunk
+    bool closed = false;          // the step's end marker has been issued
+    int step = 0;
+    auto draw = [&]() -> unsigned { return atomicAdd(&bs->ctr[step & 3], 1u); };
+    auto acquire_maps = [&](int i) {
+        if (i < kFenceWords * 32) {
+            if (fenced[i >> 5] & (1u << (i & 31))) return;
+            fenced[i >> 5] |= 1u << (i & 31);
+        }
+        for (int m = 0; m < kMapsPerInst; ++m) fence_tensormap_acquire(&maps[(size_t)i * kMapsPerInst + m]);
+    };
+    auto produce = [&]() {
+        const int s = (int)(qi % S);
+        if (cur >= nchunks) {
+            meta[s].inst = -1;
+            mbar_arrive(&full[s]);
+            closed = true;
+            ++qi;
+            return;
+        }
+        const BlockRef br = blocks[(size_t)cur * kChunk + j];
+        meta[s] = br;
+        T* dstp = ring + (size_t)s * SLOT_ELEMS;
+        unsigned char* colp = colbase + (size_t)s * SM::COL_STRIDE;
+        unsigned char* rowp = rowbase + (size_t)s * SM::ROW_STRIDE;
+        const int xb = br.x0 - VX;
+        if ((smem_u32(dstp) & 127u) != 0u || ((xb * (int)sizeof(T)) & 15) != 0 ||
+            (br.colx >= 0 && ((br.colx * (int)sizeof(T)) & 15) != 0)) {
+            atomicExch(err, 2);
+        } else {
+            acquire_maps(br.inst);
+            const CUtensorMap* m = &maps[(size_t)br.inst * kMapsPerInst + 3 * (step & 1)];
+            const uint32_t bytes =
+                TT::SLOT_BYTES + (br.colx >= 0 ? SM::COL_BYTES : 0u) + (br.rowy >= 0 ? SM::ROW_BYTES : 0u);
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&full[s], bytes);
+            tma_load_2d(dstp, &m[0], &full[s], xb, br.y0 - 1);
+            if (br.colx >= 0) tma_load_2d(colp, &m[1], &full[s], br.colx, br.y0 - 1);
+            if (br.rowy >= 0) tma_load_2d(rowp, &m[2], &full[s], xb, br.rowy);
+        }
+        ++qi;
+        if (++j == kChunk || (size_t)cur * kChunk + j >= (size_t)nblocks) {
+            cur = pf;
+            j = 0;
+            if (cur < nchunks) {
+                pf = draw();
+                // the next chunk's descriptors, one block ahead of their first use
+                asm volatile("prefetch.L1 [%0];" ::"l"(blocks + (size_t)cur * kChunk));
             }
         }
-        if (step + 1 < nsteps) {
-            if (!grid_barrier(bs, gridDim.x, err, injector && step == 0)) return;
+    };
+
+    int64_t q = 0;  // next sequence number to consume
+    bool failed = false;
+    for (step = 0; step < nsteps && !failed; ++step) {
+        const T* src = (step & 1) ? B : A;
+        T* dst = (step & 1) ? A : B;
+        (void)src;
+        if (tid == 0) {
+            cur = draw();
+            pf = cur < nchunks ? draw() : cur;
+            j = 0;
+            closed = false;
+            for (int k = 0; k < S && !closed; ++k) produce();
         }
+        for (;;) {
+            const int s = (int)(q % S);
+            const bool ok = mbar_wait(&full[s], (uint32_t)((q / S) & 1));
+            ++q;
+            const BlockRef br = meta[s];
+            if (!ok || br.inst < 0) {
+                failed = __syncthreads_or(!ok);
+                break;
+            }
+            const DevInst<T>* in = &inst[br.inst];
+            batch_block_any<T>(ring + (size_t)s * SLOT_ELEMS,
+                               reinterpret_cast<const T*>(colbase + (size_t)s * SM::COL_STRIDE),
+                               reinterpret_cast<const T*>(rowbase + (size_t)s * SM::ROW_STRIDE), dst + in->off,
+                               in->n, in->bc, in->ld, in->c, br);
+            failed = __syncthreads_or(!ok);
+            if (failed) break;
+            if (tid == 0 && !closed) produce();
+        }
+        if (!failed && step + 1 < nsteps && !grid_barrier(bs, gridDim.x, step, err, injector && step == 0))
+            failed = true;
     }
+    if (failed && tid == 0) {
+        atomicExch(err, 1);
+        // let the newest fill of every slot land (bounded wait) before the CTA exits
+        for (int64_t k = qi > S ? qi - S : 0; k < qi; ++k) mbar_wait(&full[(int)(k % S)], (uint32_t)((k / S) & 1));
+    }
+    __syncthreads();
 }
 
 }  // namespace acs
@@ -150,12 +357,12 @@ using namespace acs;
 struct acs_batch {
     int count, dtype;
     size_t esize;
-    std::vector<int64_t> n, off;
+    std::vector<int64_t> n, off, ld;
     std::vector<double> eps, dt, h;
     std::vector<int> bc;
     std::vector<DevInst<float>> inf;
     std::vector<DevInst<double>> ind;
-    int total_tiles;
+    std::vector<BlockRef> blocks;
     int64_t numel;
     // bound
     bool bound;
@@ -164,6 +371,8 @@ struct acs_batch {
     cudaStream_t stream, cap;
     char* other;
     void* dinst;
+    CUtensorMap* maps;
+    BlockRef* dblocks;
     BarrierState* bs;
     int* err;
     RedPartial* partials;
@@ -178,8 +387,14 @@ size_t al(size_t x) { return (x + kA - 1) / kA * kA; }
 size_t inst_bytes(const acs_batch* b) {
     return al((size_t)b->count * (b->dtype == ACS_F32 ? sizeof(DevInst<float>) : sizeof(DevInst<double>)));
 }
+// work buffer: the second state buffer, instances, tensor maps (six per instance),
+// block list, barrier + error flag, reduction partials, per-instance results
 size_t off_inst(const acs_batch* b) { return al((size_t)b->numel * b->esize); }
-size_t off_bar(const acs_batch* b) { return off_inst(b) + inst_bytes(b); }
+size_t off_maps(const acs_batch* b) { return off_inst(b) + inst_bytes(b); }
+size_t off_blocks(const acs_batch* b) {
+    return off_maps(b) + al(sizeof(CUtensorMap) * kMapsPerInst * (size_t)b->count);
+}
+size_t off_bar(const acs_batch* b) { return off_blocks(b) + al(sizeof(BlockRef) * b->blocks.size()); }
 size_t off_part(const acs_batch* b) { return off_bar(b) + kA; }
 size_t off_res(const acs_batch* b) { return off_part(b) + al(sizeof(RedPartial) * kMaxRedBlocks); }
 size_t total_bytes(const acs_batch* b) { return off_res(b) + al(sizeof(double) * 2 * (size_t)b->count); }
@@ -191,20 +406,21 @@ void drop_graphs(acs_batch* b) {
 
 template <typename T>
 cudaError_t launch_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
-    using TT = Tile2<T>;
     auto kern = k_batch2d<T>;
-    const size_t smem = 2 * TT::N * sizeof(T);
+    const size_t smem = BatchSmem<T>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     T* A = (T*)b->phi;
     T* B = (T*)b->other;
     const DevInst<T>* in = (const DevInst<T>*)b->dinst;
-    int count = b->count, tiles = b->total_tiles, ns = (int)nsteps;
-    void* args[] = {&A, &B, &in, &count, &tiles, &ns, &b->bs, &b->err};
+    const CUtensorMap* maps = b->maps;
+    const BlockRef* blocks = b->dblocks;
+    int count = b->count, nblocks = (int)b->blocks.size(), ns = (int)nsteps;
+    void* args[] = {&A, &B, &in, &maps, &count, &blocks, &nblocks, &ns, &b->bs, &b->err};
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)b->grid);
-    cfg.blockDim = dim3(TT::THREADS);
+    cfg.blockDim = dim3(32, 8);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -221,7 +437,10 @@ cudaError_t enqueue_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
     const int64_t chunk_max = 1 << 20;
     for (int64_t done = 0; done < nsteps;) {
         const int64_t k = std::min(chunk_max, nsteps - done);
-        cudaError_t e = b->dtype == ACS_F32 ? launch_batch<float>(b, k, st) : launch_batch<double>(b, k, st);
+        // fresh ticket counters for the launch's first steps
+        cudaError_t e = cudaMemsetAsync(b->bs->ctr, 0, sizeof(b->bs->ctr), st);
+        if (e != cudaSuccess) return e;
+        e = b->dtype == ACS_F32 ? launch_batch<float>(b, k, st) : launch_batch<double>(b, k, st);
         if (e != cudaSuccess) return e;
         if (k & 1) {
             e = cudaMemcpyAsync(b->phi, b->other, (size_t)b->numel * b->esize, cudaMemcpyDeviceToDevice, st);
@@ -234,28 +453,57 @@ cudaError_t enqueue_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
 
 template <typename T>
 void fill_inst(acs_batch* b, std::vector<DevInst<T>>& v) {
-    using TT = Tile2<T>;
+    using TT = BatchTile<T>;
     v.resize(b->count);
-    int tile0 = 0;
+    b->blocks.clear();
     for (int i = 0; i < b->count; ++i) {
         DevInst<T>& d = v[i];
         std::memset(&d, 0, sizeof(d));
         d.off = b->off[i];
-        d.nx = (int)b->n[i];
-        d.ny = (int)b->n[i];
+        d.n = (int)b->n[i];
+        d.ld = (int)b->ld[i];
         d.bc = b->bc[i];
-        const int ntx = (d.nx + TT::TX - 1) / TT::TX;
-        d.nty = (d.ny + TT::TY - 1) / TT::TY;
-        d.ntiles = ntx * d.nty;
-        d.tile0 = tile0;
-        tile0 += d.ntiles;
         const double lam = b->eps[i] * b->eps[i] * b->dt[i] / (b->h[i] * b->h[i]);
         double dmp, den;
         acs_dt_max(2, b->eps[i], b->h[i], &dmp, &den);
         const bool mp_ok = b->dt[i] <= dmp * (1.0 + 1e-12);
         d.c = make_coef<T>(2, lam, b->dt[i], ACS_SCHEME_RLB_MIE_FD, mp_ok);
+        // down each column strip, strip after strip (consecutive blocks share halo rows)
+        const int n = d.n;
+        for (int x0 = 0; x0 < n; x0 += TT::TX)
+            for (int y0 = 0; y0 < n; y0 += TT::TY) {
+                BlockRef r{i, x0, y0, -1, -1, 0, 0, 0};
+                if (d.bc == ACS_BC_PERIODIC) {
+                    // wrapped column / row from a side box unless the main box holds it
+                    if (x0 == 0 && n > TT::TX + TT::VX) r.colx = (n - 1) / TT::VX * TT::VX;
+                    if (x0 > 0 && n - 1 < x0 + TT::TX) r.colx = 0;
+                    if (y0 == 0 && n - 1 > TT::TY) r.rowy = n - 1;
+                    if (y0 > 0 && n - 1 < y0 + TT::TY) r.rowy = 0;
+                }
+                b->blocks.push_back(r);
+            }
     }
-    b->total_tiles = tile0;
+}
+
+// Six tensor maps per instance, three per state buffer (phi, then the other one):
+// the main halo box (BW x BH), the column box (VX x BH) and the row box (BW x 1) of
+// periodic wraps; n x n values, rows ld apart.
+template <typename T>
+bool encode_maps(acs_batch* b, std::vector<CUtensorMap>& maps) {
+    using TT = BatchTile<T>;
+    maps.resize((size_t)kMapsPerInst * b->count);
+    const uint32_t boxes[3][2] = {{(uint32_t)TT::BW, (uint32_t)TT::BH}, {(uint32_t)TT::VX, (uint32_t)TT::BH},
+                                  {(uint32_t)TT::BW, 1u}};
+    for (int i = 0; i < b->count; ++i)
+        for (int buf = 0; buf < 2; ++buf)
+            for (int k = 0; k < 3; ++k) {
+                const char* basep = (buf == 0 ? b->phi : b->other) + b->off[i] * (int64_t)b->esize;
+                const uint64_t dims[2] = {(uint64_t)b->n[i], (uint64_t)b->n[i]};
+                if (!encode_tensor_map(&maps[(size_t)i * kMapsPerInst + 3 * buf + k], (int)sizeof(T), 2, basep, dims,
+                                       boxes[k], (uint64_t)b->ld[i] * sizeof(T)))
+                    return false;
+            }
+    return true;
 }
 
 }  // namespace
@@ -266,14 +514,15 @@ ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, con
                              const int* bc, int dtype, acs_batch** out) {
     if (!out || count < 1 || !n || !eps || !dt || !h || !bc) return ACS_E_INVAL;
     if (dtype != ACS_F32 && dtype != ACS_F64) return ACS_E_INVAL;
-    int64_t numel = 0, tiles = 0;
+    const int64_t vx = dtype == ACS_F32 ? 4 : 2;  // values per 16 bytes
+    int64_t numel = 0, blocks = 0;
     for (int i = 0; i < count; ++i) {
         if (n[i] < 1 || n[i] > (1 << 20)) return ACS_E_INVAL;
         if (!std::isfinite(eps[i]) || !std::isfinite(dt[i]) || !std::isfinite(h[i])) return ACS_E_INVAL;
         if (eps[i] < 0 || !(h[i] > 0) || !(dt[i] > 0) || !(dt[i] < 2) || bc[i] < 0 || bc[i] > 2) return ACS_E_INVAL;
-        numel += n[i] * n[i];
-        tiles += ((n[i] + 63) / 64) * ((n[i] + 15) / 16);  // the FP64 tile (64 x 16) bounds both
-        if (numel > (int64_t(1) << 40) || tiles > 0x7fffffff) return ACS_E_INVAL;
+        numel += (n[i] + vx - 1) / vx * vx * n[i];
+        blocks += ((n[i] + 32 * vx - 1) / (32 * vx)) * ((n[i] + 15) / 16);
+        if (numel > (int64_t(1) << 40) || blocks > 0x7fffffff) return ACS_E_INVAL;
     }
     acs_batch* b = new (std::nothrow) acs_batch();
     if (!b) return ACS_E_NOMEM;
@@ -288,9 +537,11 @@ ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, con
         b->dt.push_back(dt[i]);
         b->h.push_back(h[i]);
         b->bc.push_back(bc[i]);
+        // rows padded to a 16-byte multiple, so every instance starts 16-byte aligned
+        const int64_t ldi = (n[i] + vx - 1) / vx * vx;
+        b->ld.push_back(ldi);
         b->off.push_back(b->numel);
-        // instances start on 16-byte boundaries
-        b->numel += (n[i] * n[i] + 3) / 4 * 4;
+        b->numel += ldi * n[i];
         double dmp, den;
         acs_dt_max(2, eps[i], h[i], &dmp, &den);
         if (dt[i] > den * (1.0 + 1e-12)) warn = ACS_WARN_ENERGY_CONDITION;
@@ -314,6 +565,12 @@ ACS_API int acs_batch_offsets(const acs_batch* b, int64_t* offsets) {
     return ACS_OK;
 }
 
+ACS_API int acs_batch_row_strides(const acs_batch* b, int64_t* row_strides) {
+    if (!b || !row_strides) return ACS_E_INVAL;
+    for (int i = 0; i < b->count; ++i) row_strides[i] = b->ld[i];
+    return ACS_OK;
+}
+
 ACS_API size_t acs_batch_work_bytes(const acs_batch* b) { return b ? total_bytes(b) : 0; }
 
 ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_bytes, void* stream) {
@@ -321,36 +578,49 @@ ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_
     if (work_bytes < total_bytes(b)) return ACS_E_NOMEM;
     if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return ACS_E_CUDA;
     drop_graphs(b);
+    b->bound = false;
     b->phi = (char*)d_phi;
     b->work = (char*)d_work;
     b->other = b->work;
     b->stream = (cudaStream_t)stream;
     b->dinst = b->work + off_inst(b);
+    b->maps = (CUtensorMap*)(b->work + off_maps(b));
+    b->dblocks = (BlockRef*)(b->work + off_blocks(b));
     b->bs = (BarrierState*)(b->work + off_bar(b));
     b->err = (int*)((char*)b->bs + 64);
     b->partials = (RedPartial*)(b->work + off_part(b));
     b->results = (double*)(b->work + off_res(b));
+    std::vector<CUtensorMap> maps;
+    const bool enc = b->dtype == ACS_F32 ? encode_maps<float>(b, maps) : encode_maps<double>(b, maps);
+    if (!enc) return ACS_E_UNSUPPORTED;
     const void* host = b->dtype == ACS_F32 ? (const void*)b->inf.data() : (const void*)b->ind.data();
     const size_t ib = (size_t)b->count * (b->dtype == ACS_F32 ? sizeof(DevInst<float>) : sizeof(DevInst<double>));
-    if (cudaMemcpyAsync(b->dinst, host, ib, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) return ACS_E_CUDA;
-    if (cudaMemsetAsync(b->bs, 0, kA, b->stream) != cudaSuccess) return ACS_E_CUDA;
+    if (cudaMemcpyAsync(b->dinst, host, ib, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->dblocks, b->blocks.data(), sizeof(BlockRef) * b->blocks.size(), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->bs, 0, kA, b->stream) != cudaSuccess)
+        return ACS_E_CUDA;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return ACS_E_CUDA;
-    // persistent grid: every SM's resident CTAs, never more than the tiles
+    // persistent grid: every SM's resident CTAs, never more than the chunks of blocks
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
     if (b->dtype == ACS_F32) {
-        const size_t smem = 2 * Tile2<float>::N * sizeof(float);
-        cudaFuncSetAttribute(k_batch2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<float>, Tile2<float>::THREADS, smem);
+        cudaFuncSetAttribute(k_batch2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BatchSmem<float>::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<float>, 256, BatchSmem<float>::BYTES);
     } else {
-        const size_t smem = 2 * Tile2<double>::N * sizeof(double);
-        cudaFuncSetAttribute(k_batch2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<double>, Tile2<double>::THREADS, smem);
+        cudaFuncSetAttribute(k_batch2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BatchSmem<double>::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<double>, 256,
+                                                          BatchSmem<double>::BYTES);
     }
     if (e != cudaSuccess || per_sm < 1) return ACS_E_CUDA;
-    b->grid = (int)std::min<int64_t>((int64_t)sms * per_sm, b->total_tiles);
+    const int64_t chunks = ((int64_t)b->blocks.size() + kChunk - 1) / kChunk;
+    b->grid = (int)std::min<int64_t>((int64_t)sms * per_sm, chunks);
     b->bound = true;
     return ACS_OK;
 }
@@ -388,8 +658,11 @@ ACS_API int acs_batch_observe(acs_batch* b, double* h_energy, double* h_maxnorm)
     if (!b || !h_energy || !h_maxnorm) return ACS_E_INVAL;
     if (!b->bound) return ACS_E_STATE;
     for (int i = 0; i < b->count; ++i) {
+        // rows ld apart: the reduction walks the first n values of each row
         const int64_t nn[2] = {b->n[i], b->n[i]};
-        const Geo g = make_geo(2, nn);
+        Geo g = make_geo(2, nn);
+        g.sy = b->ld[i];
+        g.sz = b->ld[i] * b->n[i];
         cudaError_t e;
         if (b->dtype == ACS_F32)
             e = launch_reduce<float>(2, b->bc[i], (const float*)b->phi + b->off[i], g, b->eps[i] * b->eps[i], b->h[i],

@@ -27,22 +27,28 @@ __global__ void __launch_bounds__(256) k_step2d(const T* __restrict__ src, T* __
         x0 = (t / nty) * TT::TX;
         y0 = (t % nty) * TT::TY;
     };
-    int x0, y0;
-    origin(t0, x0, y0);
-    stage_tile<T>(base, src, ny, nx, BC, x0, y0);
-    cp_async_commit();
-    for (int t = t0; t < t1; ++t) {
-        const int cur = (t - t0) & 1;
-        if (t + 1 < t1) {
-            int nx0, ny0;
-            origin(t + 1, nx0, ny0);
-            stage_tile<T>(base + (cur ^ 1) * TT::N, src, ny, nx, BC, nx0, ny0);
+    // ring of DEPTH staged tiles: tile t lives in buffer (t - t0) % DEPTH
+#pragma unroll
+    for (int k = 0; k < TT::DEPTH - 1; ++k) {
+        if (t0 + k < t1) {
+            int x0, y0;
+            origin(t0 + k, x0, y0);
+            stage_tile<T>(base + k * TT::N, src, ny, nx, BC, x0, y0);
         }
         cp_async_commit();
-        cp_async_wait<1>();
+    }
+    for (int t = t0; t < t1; ++t) {
+        if (t + TT::DEPTH - 1 < t1) {
+            int x0, y0;
+            origin(t + TT::DEPTH - 1, x0, y0);
+            stage_tile<T>(base + ((t + TT::DEPTH - 1 - t0) % TT::DEPTH) * TT::N, src, ny, nx, BC, x0, y0);
+        }
+        cp_async_commit();
+        cp_async_wait<TT::DEPTH - 1>();
         __syncthreads();
+        int x0, y0;
         origin(t, x0, y0);
-        update_tile<T, SOLVE>(base + cur * TT::N, dst, ny, nx, x0, y0, c);
+        update_tile<T, SOLVE>(base + ((t - t0) % TT::DEPTH) * TT::N, dst, ny, nx, x0, y0, c);
         __syncthreads();
     }
 }
@@ -59,7 +65,7 @@ cudaError_t launch_step2d(int bc, const T* src, T* dst, const Geo& g, const Coef
     if (ntiles > 0x7fffffff) return cudaErrorNotSupported;
     if (per_cta <= 0) per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(16, ntiles / (152 * 6)));
     const int grid = (int)((ntiles + per_cta - 1) / per_cta);
-    const size_t smem = 2 * TT::N * sizeof(T);
+    const size_t smem = TT::DEPTH * TT::N * sizeof(T);
     cudaError_t e = cudaSuccess;
 #define ACS_2D_CASE(B)                                                                               \
     if (bc == B) {                                                                                   \

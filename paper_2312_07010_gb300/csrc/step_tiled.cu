@@ -23,7 +23,7 @@ cudaError_t launch_step2d_tma(int bc, const T* src, T* dst, const Geo& g, const 
                               int ybchunk, int* err, cudaStream_t st);
 
 bool encode_tensor_map(CUtensorMap* map, int esize, int rank, const void* base, const uint64_t* dims,
-                       const uint32_t* box) {
+                       const uint32_t* box, uint64_t row_pitch) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -43,7 +43,7 @@ bool encode_tensor_map(CUtensorMap* map, int esize, int rank, const void* base, 
         bx[i] = box[i];
         es[i] = 1;
         if (i > 0) gs[i - 1] = stride;
-        stride *= dims[i];
+        stride = (i == 0 && row_pitch) ? row_pitch : stride * dims[i];
     }
     const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -153,7 +153,8 @@ constexpr int kNumTileVariants = 3;
 // xi^2 <= fast2max, the series is evaluated without per-point checks and (when the
 // rounding guard is on) clamped with plain min/max: fast2max keeps |xi| <= 1 + 8 ulp,
 // where the exact root is within [-1, 1] to rounding, so this gives the same values
-// as the per-point path.  Otherwise every point takes cubic_root().
+// as the per-point path.  The Newton solve does the same once every point is within
+// its seed's range.  Otherwise every point takes cubic_root().
 template <typename T, int SOLVE, int N>
 __device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<T>& c) {
     if (SOLVE == kSolveFex) {
@@ -180,6 +181,51 @@ __device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<
                 if (c.clamp) th = fmin(fmax(th, T(-1)), T(1));
                 out[i] = th;
             }
+            return;
+        }
+    }
+    if (SOLVE == kSolveNewton) {
+        // the same seed and corrections as cubic_root(), decided once for all N
+        // points: every point within its seed's range and, with the rounding guard
+        // on, every |xi| <= 1 + 8 ulp (fast2max), where min/max is the guard
+        T th[N];
+        bool ok;
+        if (c.seed == 0) {
+            T my = T(0), m2 = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const T x = xi[i] * c.rb;
+                const T y = (c.t * x) * x;
+                my = nanmax(my, y);
+                m2 = nanmax(m2, xi[i] * xi[i]);
+                th[i] = newton_seed3(x, y);
+            }
+            ok = my <= c.ymax && m2 <= c.fast2max;
+        } else {
+            T m2 = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const T x2 = xi[i] * xi[i];
+                m2 = nanmax(m2, x2);
+                th[i] = newton_seed_rational(xi[i], x2, c);
+            }
+            ok = m2 <= c.xi2max && m2 <= c.fast2max;
+        }
+        if (ok) {
+#pragma unroll
+            for (int k = 0; k < NewtonMax<T>::value; ++k) {
+                if (k < c.newton) {
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        const T th2 = th[i] * th[i];
+                        const T p = dfma(dfma(c.a, th2, c.b), th[i], -xi[i]);
+                        const T dp = dfma(c.three_a, th2, c.b);
+                        th[i] = dfma(-p, arcp(dp), th[i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) out[i] = c.clamp ? fmin(fmax(th[i], T(-1)), T(1)) : th[i];
             return;
         }
     }

@@ -22,6 +22,7 @@ struct Tile2 {
     static constexpr int BH = TY + 2;               // staged rows (one-cell halo)
     static constexpr int N = BW * BH;               // staged values (halo columns beyond one cell unused)
     static constexpr int THREADS = 256;
+    static constexpr int DEPTH = 3;                 // staged tiles in flight (ring of buffers)
 };
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
@@ -38,26 +39,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Source index of staged position (gy, gx) in a ny x nx grid, or -1 for "zero":
-// the box itself, the ghost ring by the boundary rule (wrap / mirror / zero), and
-// zero for positions beyond the ghost ring (never read by a stored point).
-__device__ __forceinline__ int64_t ghost_index(int gy, int gx, int ny, int nx, int bc) {
-    if (gy < -1 || gy > ny || gx < -1 || gx > nx) return -1;
-    const bool oy = gy < 0 || gy >= ny, ox = gx < 0 || gx >= nx;
-    if (oy && ox) return -1;  // corner: the 5-point stencil never reads it
-    if (oy || ox) {
-        if (bc == ACS_BC_DIRICHLET) return -1;
-        if (bc == ACS_BC_NEUMANN) {
-            gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
-            gx = gx < 0 ? 0 : (gx >= nx ? nx - 1 : gx);
-        } else {
-            gy = gy < 0 ? ny - 1 : (gy >= ny ? 0 : gy);
-            gx = gx < 0 ? nx - 1 : (gx >= nx ? 0 : gx);
-        }
-    }
-    return (int64_t)gy * nx + gx;
-}
-
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
     if (sizeof(T) == 4) cp_async4(dst, src, valid);
@@ -66,24 +47,33 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) 
 
 // Stage the tile at (x0, y0) of a ny x nx grid (one-cell halo included) into `buf`:
 // staged column c holds grid column x0 - VX + c; only columns VX - 1 .. VX + TX are used.
+// Warps take staged rows in turn and lanes walk a row, so addresses are a base plus the
+// lane; the ghost rule applies to whole ghost rows and to the two ends of a row.
 template <typename T>
 __device__ __forceinline__ void stage_tile(T* buf, const T* __restrict__ src, int ny, int nx, int bc, int x0,
                                            int y0) {
     using TT = Tile2<T>;
     constexpr int W = TT::TX + 2;  // used columns per staged row
-    const bool interior = x0 >= 1 && y0 >= 1 && x0 + TT::TX + 1 <= nx && y0 + TT::TY + 1 <= ny;
-    if (interior) {
-        // no ghost logic: every used position is a grid point
-        for (int i = threadIdx.x; i < W * TT::BH; i += TT::THREADS) {
-            const int r = i / W, cc = i - r * W;
-            cp_async_elem(buf + r * TT::BW + (TT::VX - 1) + cc, src + (int64_t)(y0 - 1 + r) * nx + (x0 - 1 + cc),
-                          true);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < TT::BH; r += TT::THREADS / 32) {
+        int gy = y0 - 1 + r;
+        bool rowok = true;
+        if (gy < 0 || gy >= ny) {
+            if (bc == ACS_BC_DIRICHLET || gy < -1 || gy > ny) rowok = false;
+            else if (bc == ACS_BC_NEUMANN) gy = gy < 0 ? 0 : ny - 1;
+            else gy = gy < 0 ? ny - 1 : 0;
         }
-    } else {
-        for (int i = threadIdx.x; i < W * TT::BH; i += TT::THREADS) {
-            const int r = i / W, cc = i - r * W;
-            const int64_t j = ghost_index(y0 - 1 + r, x0 - 1 + cc, ny, nx, bc);
-            cp_async_elem(buf + r * TT::BW + (TT::VX - 1) + cc, src + (j < 0 ? 0 : j), j >= 0);
+        const T* row = src + (int64_t)(rowok ? gy : 0) * nx;
+        T* out = buf + r * TT::BW + (TT::VX - 1);
+        for (int cc = lane; cc < W; cc += 32) {
+            int gx = x0 - 1 + cc;
+            bool ok = rowok;
+            if (gx < 0 || gx >= nx) {
+                if (bc == ACS_BC_DIRICHLET || gx < -1 || gx > nx) ok = false;
+                else if (bc == ACS_BC_NEUMANN) gx = gx < 0 ? 0 : nx - 1;
+                else gx = gx < 0 ? nx - 1 : 0;
+            }
+            cp_async_elem(out + cc, row + (ok ? gx : 0), ok);
         }
     }
 }

@@ -41,6 +41,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// Plain arrival (no transaction bytes): completes a phase whose count is 1.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -81,9 +86,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
 }
 
 // Host: encode a tiled tensor map of `rank` dimensions (dims[0] fastest) with the
-// given box, FP32 or FP64 elements, zero fill out of bounds.  Returns false if the
-// driver entry point is unavailable or the encoding is rejected.
+// given box, FP32 or FP64 elements, zero fill out of bounds.  Rows are dims[0]
+// elements apart unless row_pitch (bytes, a multiple of 16) is given; higher
+// dimensions follow densely.  Returns false if the driver entry point is unavailable
+// or the encoding is rejected.
 bool encode_tensor_map(CUtensorMap* map, int esize, int rank, const void* base, const uint64_t* dims,
-                       const uint32_t* box);
+                       const uint32_t* box, uint64_t row_pitch = 0);
+
+// Make a tensor map that was written to global memory (by a host copy before the
+// launch) visible to the TMA unit of this thread before its first use.
+__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(map) : "memory");
+}
 
 }  // namespace acs

@@ -14,7 +14,7 @@ from typing import Optional, Sequence, Tuple
 import numpy as np
 import torch
 
-from ._lib import (ACS_F32, ACS_F64, ACS_KERNEL_AUTO, AcsError, check, lib)
+from ._lib import (ACS_F32, ACS_F64, ACS_KERNEL_AUTO, ACS_KERNEL_LB, AcsError, check, lib)
 
 _DT = {"f32": (ACS_F32, torch.float32, np.float32), "f64": (ACS_F64, torch.float64, np.float64)}
 
@@ -117,6 +117,14 @@ class AllenCahn:
         d = ctypes.c_int()
         check(self.L.acs_get_kernel(self.ctx, ctypes.byref(k), ctypes.byref(d)), "acs_get_kernel")
         return k.value, d.value
+
+    def use_lb_form(self, omega1: float = 0.0) -> None:
+        """Step with the collide-and-stream population form (acs_lb_bind + ACS_KERNEL_LB):
+        allocates the (2d+1) population arrays; omega1 = 0 takes the paper's weight."""
+        nb = int(self.L.acs_lb_bytes(self.ctx))
+        self._pop = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        check(self.L.acs_lb_bind(self.ctx, ctypes.c_void_p(self._pop.data_ptr()), nb, float(omega1)), "acs_lb_bind")
+        self.set_kernel(ACS_KERNEL_LB)
 
     def set_scheme(self, scheme: int) -> None:
         check(self.L.acs_set_scheme(self.ctx, int(scheme)), "acs_set_scheme")

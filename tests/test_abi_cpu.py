@@ -117,3 +117,30 @@ def test_unbound_context_rejects_device_calls(L):
     assert L.acs_set_scheme(ctx, 5) == -1
     L.acs_destroy(ctx)
     L.acs_destroy(None)
+
+
+def test_lb_form_host_logic(L):
+    """Population form: buffer size (2d+1) n^d elements; weight and order checks.
+    The pointer is never dereferenced by these calls (no device work)."""
+    fake = ctypes.c_void_p(1 << 20)
+    for dims, n in ((1, (40,)), (2, (12, 10)), (3, (6, 5, 4))):
+        for dtype, es in ((0, 4), (1, 8)):
+            rc, ctx = _create(L, dims, n, 0.02, 0.01, 0.1, 1, dtype)
+            assert rc == 0
+            tot = math.prod(n)
+            assert L.acs_lb_bytes(ctx) == (2 * dims + 1) * tot * es
+            # selecting the form before binding its buffer is out of order
+            assert L.acs_set_kernel(ctx, 4, 1) == -6
+            nb = L.acs_lb_bytes(ctx)
+            assert L.acs_lb_bind(ctx, fake, nb - 1, 0.0) == -3
+            assert L.acs_lb_bind(ctx, fake, nb, 1.0 / (2 * dims) * 1.01) == -1
+            assert L.acs_lb_bind(ctx, ctypes.c_void_p((1 << 20) + 4), nb, 0.0) == -1
+            assert L.acs_lb_bind(ctx, fake, nb, math.nan) == -1
+            assert L.acs_lb_bind(ctx, fake, nb, 0.0) == 0
+            assert L.acs_set_kernel(ctx, 4, 1) == 0
+            k, d = ctypes.c_int(), ctypes.c_int()
+            assert L.acs_get_kernel(ctx, ctypes.byref(k), ctypes.byref(d)) == 0 and k.value == 4
+            # the population form exists for the paper's scheme only
+            assert L.acs_set_scheme(ctx, 1) == -7
+            assert L.acs_set_scheme(ctx, 0) == 0
+            L.acs_destroy(ctx)

@@ -46,6 +46,40 @@ def test_batch_equals_standalone_fp32(acs, steps):
         assert E[k] == pytest.approx(s.energy(), rel=1e-12) and M[k] == s.maxnorm()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_ragged_small_sides(acs, dtype):
+    """Sides that end mid-vector, are smaller than one vector, or straddle a block
+    edge, under every boundary: each instance equals its standalone run bit for bit."""
+    sides = [1, 2, 3, 5, 7, 8, 9, 63, 65, 127, 129, 131, 132, 133]
+    n, eps, dt, h, bc = [], [], [], [], []
+    for k, m in enumerate(sides):
+        for b in (0, 1, 2):
+            hh = 1.0 / (m + 1) if b == 2 else 1.0 / m
+            e = 0.02 + 0.001 * k
+            n.append(m)
+            eps.append(e)
+            h.append(hh)
+            dt.append(acs.dt_max(2, e, hh)[0] * 0.9)
+            bc.append(b)
+    bt = acs.Batch(n, eps, dt, h, bc, dtype)
+    nd = np.float32 if dtype == "f32" else np.float64
+    rng = np.random.default_rng(11)
+    phi0 = [rng.uniform(-1, 1, size=(m, m)).astype(nd) for m in n]
+    bt.set_states(phi0)
+    vx = 4 if dtype == "f32" else 2
+    assert bt.ld == [(m + vx - 1) // vx * vx for m in n]
+    assert all(o % vx == 0 for o in bt.offsets)
+    bt.step(5)
+    got = bt.states()
+    for k in range(len(n)):
+        s = acs.AllenCahn((n[k], n[k]), eps[k], dt[k], h[k], bc[k], dtype)
+        s.set_state(phi0[k])
+        s.step(5)
+        assert np.array_equal(got[k], s.numpy()), (n[k], bc[k])
+        # the strided device view holds the same state
+        assert np.array_equal(bt.view(k).cpu().numpy(), got[k])
+
+
 def test_batch_fp64_vs_oracle(acs):
     inst = _instances(6, 9, 16, 200)
     b = acs.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],

@@ -159,6 +159,35 @@ def test_large_dt_robust_cubic(acs):
     assert worst > 1.0
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("dims,shape", [(2, (40, 40)), (3, (24, 24, 24)), (2, (33, 50))], ids=str)
+def test_large_dt_within_maximum_principle(acs, dims, shape, dtype):
+    """dt close to Theorem 2's limit (a = dt/2 near 0.4): the cubic's series does not
+    converge over |xi| <= 1, so the Newton solve takes its rational seed.  FP64 matches
+    the oracle; the tiled and naive kernels agree bit for bit; FP32 stays within 2e-5."""
+    n = shape[-1]
+    h, eps = 1.0 / n, 0.004
+    dt = 0.98 * acs.dt_max(dims, eps, h)[0]
+    assert dt > 0.7
+    phi0 = np.random.default_rng(17).uniform(-1, 1, size=shape)
+    nd = np.float32 if dtype == "f32" else np.float64
+    a = acs.AllenCahn(shape, eps, dt, h, BC_PERIODIC, dtype)
+    b = acs.AllenCahn(shape, eps, dt, h, BC_PERIODIC, dtype)
+    a.set_kernel(acs.ACS_KERNEL_TILED)
+    b.set_kernel(acs.ACS_KERNEL_NAIVE)
+    a.set_state(phi0.astype(nd))
+    b.set_state(phi0.astype(nd))
+    a.step(40)
+    b.step(40)
+    assert np.array_equal(a.numpy(), b.numpy())
+    ref = oracle.run_fd(phi0.astype(nd), eps, dt, h, BC_PERIODIC, 40)
+    if dtype == "f64":
+        assert relerr(a.numpy(), ref) <= 1e-12
+    else:
+        assert np.abs(a.numpy() - ref).max() <= 2e-5
+    assert a.maxnorm() <= 1.0
+
+
 def test_nonfinite_state_is_reported(acs):
     shape = (16, 16)
     h, eps, dt, phi0 = _problem(shape, BC_PERIODIC, 5)
