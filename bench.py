@@ -470,6 +470,28 @@ def extras(P, args):
                                   "fwd_ms_per_time_step": ms_f / w.steps,
                                   "fwd_bwd_over_fwd": ms_fb / ms_f}
     s.close()
+    del s
+    torch.cuda.empty_cache()
+    # the collide-and-stream population form on the 512^3 workload, against the FD form:
+    # per update it writes and reads 2d+1 populations (collide: 1 read + 7 writes; stream:
+    # 7 + 1 reads + 1 write = 17 values), and keeps them resident
+    w = cfg2("f32")
+    s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    s.use_lb_form()
+    phi0 = torch.from_numpy(w.phi0().astype(np.float32)).cuda()
+    s.set_state(phi0)
+    nsteps = 20
+
+    def go_lb():
+        s.step(nsteps)
+    ms = _time(go_lb, 2)
+    glups = w.numel * nsteps / (ms * 1e-3) / 1e9
+    vals = 2 * (2 * 3 + 1) + 3
+    out["cfg2_fp32_lb_form"] = {"glups": glups, "ms_per_time_step": ms / nsteps,
+                                "alg_bytes_per_update": vals * 4, "achieved_gbs": glups * vals * 4,
+                                "hbm_frac": glups * vals * 4 / peak,
+                                "resident_arrays_lb": 2 * 3 + 2, "resident_arrays_fd": 2}
+    s.close()
     return out
 
 

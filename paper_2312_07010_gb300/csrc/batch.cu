@@ -28,8 +28,9 @@
 
 namespace acs {
 
+// One instance as the kernel sees it; copied into shared memory with each block.
 template <typename T>
-struct DevInst {
+struct alignas(16) DevInst {
     int64_t off;  // first element of the instance in the packed state
     int n;        // side (x fastest)
     int ld;       // row stride in elements (a 16-byte multiple)
@@ -37,6 +38,7 @@ struct DevInst {
     int pad;
     Coef<T> c;
 };
+static_assert(sizeof(DevInst<float>) % 16 == 0 && sizeof(DevInst<double>) % 16 == 0, "bulk-copy size");
 
 // One block of one instance.  colx / rowy: where a periodic instance's wrapped
 // column / row for this block is fetched from when the main box does not hold it
@@ -64,7 +66,10 @@ struct BatchSmem {
     static constexpr uint32_t OFF_RING = TT::BAR_BYTES;
     static constexpr uint32_t OFF_COL = OFF_RING + TT::S * TT::SLOT_STRIDE;
     static constexpr uint32_t OFF_ROW = OFF_COL + TT::S * COL_STRIDE;
-    static constexpr uint32_t OFF_META = OFF_ROW + TT::S * ROW_STRIDE;
+    static constexpr uint32_t INST_BYTES = sizeof(DevInst<T>);
+    static constexpr uint32_t INST_STRIDE = (INST_BYTES + 127u) / 128u * 128u;
+    static constexpr uint32_t OFF_INST = OFF_ROW + TT::S * ROW_STRIDE;
+    static constexpr uint32_t OFF_META = OFF_INST + TT::S * INST_STRIDE;
     static constexpr size_t BYTES = 128 + OFF_META + TT::S * sizeof(BlockRef);
 };
 
@@ -226,38 +231,56 @@ __device__ __forceinline__ void batch_block_any(const T* cur, const T* colb, con
 // barrier.  Thread 0 is the producer: it draws tickets one chunk ahead, issues each
 // block's loads into the next free slot with the block's description in `meta`, and
 // closes the step with an end marker (a slot whose mbarrier completes without data).
+// A ninth warp produces (its lane 0 only); the eight compute warps consume slots
+// independently: `full[s]` says a slot has landed, `empty[s]` (one arrival per compute
+// warp) that every warp is done with it, so no compute warp waits for another and
+// only the producer waits, before it refills a slot.
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
+__global__ void __launch_bounds__(288, 3) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
                                                  const CUtensorMap* __restrict__ maps, int count,
                                                  const BlockRef* __restrict__ blocks, int nblocks, int nsteps,
                                                  BarrierState* bs, int* err) {
     using TT = BatchTile<T>;
     using SM = BatchSmem<T>;
-    constexpr int VX = TT::VX, S = TT::S;
+    constexpr int VX = TT::VX, S = TT::S, WARPS = 8;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
+    static_assert(2 * S * sizeof(uint64_t) <= TT::BAR_BYTES, "full and empty barriers");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     uint64_t* full = reinterpret_cast<uint64_t*>(base);
+    uint64_t* empty = full + S;
     T* ring = reinterpret_cast<T*>(base + SM::OFF_RING);
     unsigned char* colbase = base + SM::OFF_COL;
     unsigned char* rowbase = base + SM::OFF_ROW;
     BlockRef* meta = reinterpret_cast<BlockRef*>(base + SM::OFF_META);
+    unsigned char* instbase = base + SM::OFF_INST;
     __shared__ unsigned fenced[kFenceWords];
+    __shared__ volatile int s_fail;
     const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int lane = threadIdx.x;
+    const bool producer = threadIdx.y == WARPS && lane == 0;
     const unsigned nchunks = (unsigned)((nblocks + kChunk - 1) / kChunk);
     if (tid < kFenceWords) fenced[tid] = 0u;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], WARPS);
+        }
         fence_mbar_init();
+        s_fail = 0;
     }
     __syncthreads();
     const bool injector = bs->inject != 0 && blockIdx.x == gridDim.x - 1;
+    auto fail = [&]() {
+        s_fail = 1;
+        atomicExch(err, 1);
+    };
 
-    // producer state (thread 0 only)
+    // producer state (the producer thread only)
     int64_t qi = 0;               // next sequence number to fill (slot qi % S, phase (qi / S) & 1)
     unsigned cur = 0, pf = 0;     // current chunk and the next one (drawn ahead)
     int j = 0;                    // next block within the current chunk
-    bool closed = false;          // the step's end marker has been issued
+    bool closed = false;          // the step's end marker has been issued (or the CTA failed)
     int step = 0;
     auto draw = [&]() -> unsigned { return atomicAdd(&bs->ctr[step & 3], 1u); };
     auto acquire_maps = [&](int i) {
@@ -269,6 +292,12 @@ __global__ void __launch_bounds__(256, 3) k_batch2d(T* A, T* B, const DevInst<T>
     };
     auto produce = [&]() {
         const int s = (int)(qi % S);
+        // every warp must be done with the slot's previous block
+        if (qi >= S && !mbar_wait(&empty[s], (uint32_t)(((qi / S) - 1) & 1))) {
+            fail();
+            closed = true;
+            return;
+        }
         if (cur >= nchunks) {
             meta[s].inst = -1;
             mbar_arrive(&full[s]);
@@ -288,10 +317,11 @@ __global__ void __launch_bounds__(256, 3) k_batch2d(T* A, T* B, const DevInst<T>
         } else {
             acquire_maps(br.inst);
             const CUtensorMap* m = &maps[(size_t)br.inst * kMapsPerInst + 3 * (step & 1)];
-            const uint32_t bytes =
-                TT::SLOT_BYTES + (br.colx >= 0 ? SM::COL_BYTES : 0u) + (br.rowy >= 0 ? SM::ROW_BYTES : 0u);
+            const uint32_t bytes = TT::SLOT_BYTES + SM::INST_BYTES + (br.colx >= 0 ? SM::COL_BYTES : 0u) +
+                                   (br.rowy >= 0 ? SM::ROW_BYTES : 0u);
             fence_proxy_async();
             mbar_arrive_expect_tx(&full[s], bytes);
+            bulk_load(instbase + (size_t)s * SM::INST_STRIDE, &inst[br.inst], SM::INST_BYTES, &full[s]);
             tma_load_2d(dstp, &m[0], &full[s], xb, br.y0 - 1);
             if (br.colx >= 0) tma_load_2d(colp, &m[1], &full[s], br.colx, br.y0 - 1);
             if (br.rowy >= 0) tma_load_2d(rowp, &m[2], &full[s], xb, br.rowy);
@@ -308,41 +338,52 @@ __global__ void __launch_bounds__(256, 3) k_batch2d(T* A, T* B, const DevInst<T>
         }
     };
 
-    int64_t q = 0;  // next sequence number to consume
+    int64_t q = 0;  // next sequence number to consume (the same in every consumer warp)
     bool failed = false;
     for (step = 0; step < nsteps && !failed; ++step) {
-        const T* src = (step & 1) ? B : A;
         T* dst = (step & 1) ? A : B;
-        (void)src;
-        if (tid == 0) {
+        if (producer) {
+            // other CTAs' stores of the previous step (ordered by the grid barrier)
+            // before this thread's async-proxy reads of them
+            asm volatile("fence.proxy.async.global;" ::: "memory");
             cur = draw();
             pf = cur < nchunks ? draw() : cur;
             j = 0;
             closed = false;
-            for (int k = 0; k < S && !closed; ++k) produce();
-        }
-        for (;;) {
-            const int s = (int)(q % S);
-            const bool ok = mbar_wait(&full[s], (uint32_t)((q / S) & 1));
-            ++q;
-            const BlockRef br = meta[s];
-            if (!ok || br.inst < 0) {
-                failed = __syncthreads_or(!ok);
-                break;
+            while (!closed) produce();
+        } else if (threadIdx.y < WARPS) {
+            for (;;) {
+                if (s_fail) break;
+                const int s = (int)(q % S);
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)((q / S) & 1)));
+                if (!ok) {
+                    if (lane == 0) fail();
+                    break;
+                }
+                ++q;
+                const BlockRef br = meta[s];
+                if (br.inst >= 0) {
+                    // the instance (copied in with the block) and its coefficients in
+                    // registers: stores to dst cannot then force them to be read again
+                    const DevInst<T>* in =
+                        reinterpret_cast<const DevInst<T>*>(instbase + (size_t)s * SM::INST_STRIDE);
+                    const Coef<T> c = in->c;
+                    batch_block_any<T>(ring + (size_t)s * SLOT_ELEMS,
+                                       reinterpret_cast<const T*>(colbase + (size_t)s * SM::COL_STRIDE),
+                                       reinterpret_cast<const T*>(rowbase + (size_t)s * SM::ROW_STRIDE),
+                                       dst + in->off, in->n, in->bc, in->ld, c, br);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+                if (br.inst < 0) break;
             }
-            const DevInst<T>* in = &inst[br.inst];
-            batch_block_any<T>(ring + (size_t)s * SLOT_ELEMS,
-                               reinterpret_cast<const T*>(colbase + (size_t)s * SM::COL_STRIDE),
-                               reinterpret_cast<const T*>(rowbase + (size_t)s * SM::ROW_STRIDE), dst + in->off,
-                               in->n, in->bc, in->ld, in->c, br);
-            failed = __syncthreads_or(!ok);
-            if (failed) break;
-            if (tid == 0 && !closed) produce();
         }
+        __syncthreads();
+        failed = s_fail != 0;
         if (!failed && step + 1 < nsteps && !grid_barrier(bs, gridDim.x, step, err, injector && step == 0))
             failed = true;
     }
-    if (failed && tid == 0) {
+    if (failed && producer) {
         atomicExch(err, 1);
         // let the newest fill of every slot land (bounded wait) before the CTA exits
         for (int64_t k = qi > S ? qi - S : 0; k < qi; ++k) mbar_wait(&full[(int)(k % S)], (uint32_t)((k / S) & 1));
@@ -420,7 +461,7 @@ cudaError_t launch_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)b->grid);
-    cfg.blockDim = dim3(32, 8);
+    cfg.blockDim = dim3(32, 9);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -611,11 +652,11 @@ ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_
     if (b->dtype == ACS_F32) {
         cudaFuncSetAttribute(k_batch2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)BatchSmem<float>::BYTES);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<float>, 256, BatchSmem<float>::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<float>, 288, BatchSmem<float>::BYTES);
     } else {
         cudaFuncSetAttribute(k_batch2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)BatchSmem<double>::BYTES);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<double>, 256,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d<double>, 288,
                                                           BatchSmem<double>::BYTES);
     }
     if (e != cudaSuccess || per_sm < 1) return ACS_E_CUDA;
