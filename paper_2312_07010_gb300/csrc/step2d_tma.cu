@@ -8,6 +8,8 @@
 // and takes its x neighbours from its registers and warp shuffles, its y neighbours
 // from shared memory.  Boundaries as in the 3D kernel: TMA zero fill for Dirichlet,
 // per-row fix-ups (own value / wrapped global read) for Neumann and periodic.
+#include <type_traits>
+
 #include "acs_host.h"
 #include "stream_tile.cuh"
 #include "tma.cuh"
@@ -15,7 +17,7 @@
 namespace acs {
 
 template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
-__global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_step2d_tma(const __grid_constant__ CUtensorMap tmap,
                                                     const T* __restrict__ src, T* __restrict__ dst, Geo g,
                                                     Coef<T> c, int ybchunk, int* err, RedPartial* part) {
     using TT = Tile3<T, RPT, SS>;
@@ -44,124 +46,128 @@ __global__ void __launch_bounds__(256) k_step2d_tma(const __grid_constant__ CUte
     }
     __syncthreads();
 
-    auto issue = [&](int b) {
-        const int k = b - b0;
-        T* dstp = ring + (size_t)(k % S) * SLOT_ELEMS;
+    // block b lives in ring slot (b - b0) % S; the loop tracks the slot and the
+    // mbarrier phase incrementally
+    auto issue = [&](int b, int slot) {
+        T* dstp = ring + (size_t)slot * SLOT_ELEMS;
         if ((smem_u32(dstp) & 127u) != 0u || (((x0 - VX) * (int)sizeof(T)) & 15) != 0) {
             atomicExch(err, 2);
             return;
         }
         fence_proxy_async();
-        mbar_arrive_expect_tx(&full[k % S], TT::SLOT_BYTES);
-        tma_load_2d(dstp, &tmap, &full[k % S], x0 - VX, b * TY - 1);
+        mbar_arrive_expect_tx(&full[slot], TT::SLOT_BYTES);
+        tma_load_2d(dstp, &tmap, &full[slot], x0 - VX, b * TY - 1);
     };
     int last_issued = min(b0 + S, b1) - 1;
     if (tid == 0)
-        for (int b = b0; b <= last_issued; ++b) issue(b);
+        for (int b = b0; b <= last_issued; ++b) issue(b, b - b0);
 
     const int64_t sy = g.sy;
+    // rows are a multiple of VX, so a thread stores its whole vector or nothing
     const bool xlo = gx == 0, xhi = gx + VX == nx;
-    const bool vecok = gx + VX <= nx;
+    const bool colok = gx < nx;
     bool failed = false;
     EnergyAcc<T> eacc;
-    for (int b = b0; b < b1 && !failed; ++b) {
-        const int k = b - b0;
-        const bool ok = mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
-        const T* cur = ring + (size_t)(k % S) * SLOT_ELEMS;
-        const int gy0 = b * TY + r0;
-        T cz[RPT][VX], below[VX], above[VX], xi[NP];
+    int sc = 0;        // slot of the current block
+    uint32_t pc = 0u;  // its mbarrier phase parity
+    const bool edge = BC != ACS_BC_DIRICHLET && (x0 == 0 || x0 + TX >= nx || b0 * TY == 0 || b1 * TY >= ny);
+    auto run = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        for (int b = b0; b < b1 && !failed; ++b) {
+            const bool ok = mbar_wait(&full[sc], pc);
+            const T* cur = ring + (size_t)sc * SLOT_ELEMS;
+            const int gy0 = b * TY + r0;
+            T cz[RPT][VX], below[VX], above[VX], xi[NP];
 #pragma unroll
-        for (int rr = 0; rr < RPT; ++rr) Vec<T>::get(cur + (r0 + rr + 1) * BW + VX + xl, cz[rr]);
-        Vec<T>::get(cur + r0 * BW + VX + xl, below);
-        Vec<T>::get(cur + (r0 + RPT + 1) * BW + VX + xl, above);
-        const bool edge = BC != ACS_BC_DIRICHLET &&
-                          (x0 == 0 || x0 + TX >= nx || b * TY == 0 || (b + 1) * TY >= ny);
+            for (int rr = 0; rr < RPT; ++rr) Vec<T>::get(cur + (r0 + rr + 1) * BW + VX + xl, cz[rr]);
+            Vec<T>::get(cur + r0 * BW + VX + xl, below);
+            Vec<T>::get(cur + (r0 + RPT + 1) * BW + VX + xl, above);
+            const bool bedge = EDGE && (x0 == 0 || x0 + TX >= nx || b * TY == 0 || (b + 1) * TY >= ny);
 #pragma unroll
-        for (int rr = 0; rr < RPT; ++rr) {
-            const int gyr = gy0 + rr;
-            T ym[VX], yp[VX];
+            for (int rr = 0; rr < RPT; ++rr) {
+                const int gyr = gy0 + rr;
+                T ym[VX], yp[VX];
 #pragma unroll
-            for (int v = 0; v < VX; ++v) {
-                ym[v] = rr == 0 ? below[v] : cz[rr - 1][v];
-                yp[v] = rr == RPT - 1 ? above[v] : cz[rr + 1][v];
-            }
-            T left = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
-            T right = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
-            if (lx == 0) left = cur[(r0 + rr + 1) * BW + VX - 1];
-            if (lx == 31) right = cur[(r0 + rr + 1) * BW + VX + TX];
-            if (edge && gyr < ny) {
-                if (gyr == 0) {
-                    if (BC == ACS_BC_NEUMANN) {
-#pragma unroll
-                        for (int v = 0; v < VX; ++v) ym[v] = cz[rr][v];
-                    } else if (gx < nx) {
-                        Vec<T>::ldg(src + (int64_t)(ny - 1) * sy + gx, ym);
-                    }
+                for (int v = 0; v < VX; ++v) {
+                    ym[v] = rr == 0 ? below[v] : cz[rr - 1][v];
+                    yp[v] = rr == RPT - 1 ? above[v] : cz[rr + 1][v];
                 }
-                if (gyr == ny - 1) {
-                    if (BC == ACS_BC_NEUMANN) {
+                // the tile's outer two x neighbours come from the halo group (every lane
+                // reads the same word: a broadcast, no branch)
+                const T hl = cur[(r0 + rr + 1) * BW + VX - 1];
+                const T hr = cur[(r0 + rr + 1) * BW + VX + TX];
+                const T su = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
+                const T sd = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
+                T left = lx == 0 ? hl : su;
+                T right = lx == 31 ? hr : sd;
+                if (bedge && gyr < ny) {
+                    if (gyr == 0) {
+                        if (BC == ACS_BC_NEUMANN) {
 #pragma unroll
-                        for (int v = 0; v < VX; ++v) yp[v] = cz[rr][v];
-                    } else if (gx < nx) {
-                        Vec<T>::ldg(src + gx, yp);
-                    }
-                }
-                if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[(int64_t)gyr * sy + nx - 1];
-                if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[(int64_t)gyr * sy];
-            }
-            if (MODE == kModeEnergy) {
-                // forward links along x and y (ghost-ruled as for the step) and the
-                // links of the first unknowns to the zero Dirichlet boundary
-                if (gyr < ny) {
-#pragma unroll
-                    for (int v = 0; v < VX; ++v) {
-                        if (gx + v >= nx) continue;
-                        const T p = cz[rr][v];
-                        eacc.point2(p, v == VX - 1 ? right : cz[rr][v + 1], yp[v]);
-                        if (BC == ACS_BC_DIRICHLET) {
-                            if (gx + v == 0) eacc.ghost_link(p);
-                            if (gyr == 0) eacc.ghost_link(p);
+                            for (int v = 0; v < VX; ++v) ym[v] = cz[rr][v];
+                        } else if (gx < nx) {
+                            Vec<T>::ldg(src + (int64_t)(ny - 1) * sy + gx, ym);
                         }
                     }
-                }
-                continue;
-            }
+                    if (gyr == ny - 1) {
+                        if (BC == ACS_BC_NEUMANN) {
 #pragma unroll
-            for (int v = 0; v < VX; ++v) {
-                const T xm = v == 0 ? left : cz[rr][v - 1];
-                const T xp = v == VX - 1 ? right : cz[rr][v + 1];
-                xi[rr * VX + v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
+                            for (int v = 0; v < VX; ++v) yp[v] = cz[rr][v];
+                        } else if (gx < nx) {
+                            Vec<T>::ldg(src + gx, yp);
+                        }
+                    }
+                    if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[(int64_t)gyr * sy + nx - 1];
+                    if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[(int64_t)gyr * sy];
+                }
+                if (MODE == kModeEnergy) {
+                    // forward links along x and y (ghost-ruled as for the step) and the
+                    // links of the first unknowns to the zero Dirichlet boundary
+                    if (gyr < ny) {
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            if (gx + v >= nx) continue;
+                            const T p = cz[rr][v];
+                            eacc.point2(p, v == VX - 1 ? right : cz[rr][v + 1], yp[v]);
+                            if (BC == ACS_BC_DIRICHLET) {
+                                if (gx + v == 0) eacc.ghost_link(p);
+                                if (gyr == 0) eacc.ghost_link(p);
+                            }
+                        }
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int v = 0; v < VX; ++v) {
+                    const T xm = v == 0 ? left : cz[rr][v - 1];
+                    const T xp = v == VX - 1 ? right : cz[rr][v + 1];
+                    xi[rr * VX + v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
+                }
             }
-        }
-        if (MODE == kModeEnergy) {
-            eacc.plane_done();
+            if (MODE == kModeEnergy) {
+                eacc.plane_done();
+            } else {
+                T out[NP];
+                roots<T, SOLVE, NP>(xi, out, c);
+                T* o = dst + (int64_t)gy0 * sy + gx;
+#pragma unroll
+                for (int rr = 0; rr < RPT; ++rr)
+                    if (colok && gy0 + rr < ny) Vec<T>::put(o + rr * sy, &out[rr * VX]);
+            }
             failed = __syncthreads_or(!ok);
+            // block b + S reuses block b's slot, free now that every thread is past it
             if (!failed && tid == 0 && b + S < b1) {
-                issue(b + S);
+                issue(b + S, sc);
                 last_issued = b + S;
             }
-            continue;
-        }
-        T out[NP];
-        roots<T, SOLVE, NP>(xi, out, c);
-        T* o = dst + (int64_t)gy0 * sy + gx;
-#pragma unroll
-        for (int rr = 0; rr < RPT; ++rr) {
-            if (gy0 + rr >= ny) continue;
-            if (vecok) {
-                Vec<T>::put(o + rr * sy, &out[rr * VX]);
-            } else {
-#pragma unroll
-                for (int v = 0; v < VX; ++v)
-                    if (gx + v < nx) o[rr * sy + v] = out[rr * VX + v];
+            if (++sc == S) {
+                sc = 0;
+                pc ^= 1u;
             }
         }
-        failed = __syncthreads_or(!ok);
-        if (!failed && tid == 0 && b + S < b1) {
-            issue(b + S);
-            last_issued = b + S;
-        }
-    }
+    };
+    if (edge) run(std::true_type());
+    else run(std::false_type());
     if (MODE == kModeEnergy) energy_block_write(eacc, part + (blockIdx.y * gridDim.x + blockIdx.x));
     if (failed) {
         if (tid == 0) {

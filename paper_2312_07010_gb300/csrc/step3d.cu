@@ -14,6 +14,8 @@
 // periodic, the edge plane itself for Neumann, an out-of-range plane -- TMA zero fill
 // -- for Dirichlet).  Along x and y the zero fill gives Dirichlet; Neumann uses the
 // point's own value and periodic reads the wrapped neighbour from global memory.
+#include <type_traits>
+
 #include "acs_host.h"
 #include "stream_tile.cuh"
 #include "tma.cuh"
@@ -21,7 +23,7 @@
 namespace acs {
 
 template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
-__global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_step3d(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src,
                                                 T* __restrict__ dst, Geo g, Coef<T> c, int ntx, int zchunk,
                                                 int* err, RedPartial* part) {
     using TT = Tile3<T, RPT, SS>;
@@ -52,10 +54,11 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
     }
     __syncthreads();
 
-    auto slot_of = [&](int p) { return ring + (size_t)((p - (z0 - 1)) % S) * SLOT_ELEMS; };
-    auto issue = [&](int p) {
-        const int k = p - (z0 - 1);
-        T* dstp = slot_of(p);
+    // plane p lives in ring slot (p - z0 + 1) % S; the z loop tracks the slot and the
+    // mbarrier phase of the current plane incrementally
+    auto slot_ptr = [&](int slot) { return ring + (size_t)slot * SLOT_ELEMS; };
+    auto issue = [&](int p, int slot) {
+        T* dstp = slot_ptr(slot);
         // self-check of the TMA preconditions: a misaligned destination or x offset is
         // recorded and the copy skipped (the consumers' bounded wait then reports it)
         if ((smem_u32(dstp) & 127u) != 0u || (((x0 - VX) * (int)sizeof(T)) & 15) != 0) {
@@ -63,12 +66,8 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
             return;
         }
         fence_proxy_async();
-        mbar_arrive_expect_tx(&full[k % S], TT::SLOT_BYTES);
-        tma_load_3d(dstp, &tmap, &full[k % S], x0 - VX, y0 - 1, zsrc<BC>(p, nz));
-    };
-    auto wait_plane = [&](int p) -> bool {
-        const int k = p - (z0 - 1);
-        return mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
+        mbar_arrive_expect_tx(&full[slot], TT::SLOT_BYTES);
+        tma_load_3d(dstp, &tmap, &full[slot], x0 - VX, y0 - 1, zsrc<BC>(p, nz));
     };
     // this thread's RPT rows x VX values of a plane
     auto read_mine = [&](const T* sl, T (&o)[RPT][VX]) {
@@ -78,138 +77,147 @@ __global__ void __launch_bounds__(256) k_step3d(const __grid_constant__ CUtensor
 
     int last_issued = min(z0 + S - 2, z1);
     if (tid == 0)
-        for (int p = z0 - 1; p <= last_issued; ++p) issue(p);
+        for (int p = z0 - 1; p <= last_issued; ++p) issue(p, (p - z0 + 1) % S);
 
     T zm[RPT][VX], cz[RPT][VX];
-    bool ok = wait_plane(z0 - 1);
-    read_mine(slot_of(z0 - 1), zm);
-    ok = wait_plane(z0) && ok;
-    read_mine(slot_of(z0), cz);
+    bool ok = mbar_wait(&full[0], 0u);
+    read_mine(slot_ptr(0), zm);
+    ok = mbar_wait(&full[1], 0u) && ok;
+    read_mine(slot_ptr(1), cz);
     bool failed = __syncthreads_or(!ok);
-    if (!failed && tid == 0 && z0 + S - 1 <= z1) issue(z0 + S - 1);
+    if (!failed && tid == 0 && z0 + S - 1 <= z1) issue(z0 + S - 1, 0);
     if (!failed) last_issued = min(z0 + S - 1, z1);
+    int sc = 1;        // slot of the current plane
+    uint32_t pc = 0u;  // its mbarrier phase parity
 
     const int64_t sy = g.sy, sz = g.sz;
-    // Boundary handling hoisted out of the z loop.  Only a CTA whose tile touches an
-    // x or y face (Neumann / periodic) takes the per-row fix-ups; Dirichlet needs none
-    // (TMA zero fill), and z faces are handled by the producer's plane choice.
+    // Boundary handling hoisted out of the z loop: only a CTA whose tile touches an
+    // x or y face (Neumann / periodic) runs the per-row fix-ups; Dirichlet needs none
+    // (TMA zero fill), and z faces are handled by the producer's plane choice.  The
+    // rows nx is a multiple of VX, so a thread stores its whole vector or nothing.
     const bool edge = BC != ACS_BC_DIRICHLET && (x0 == 0 || x0 + TX >= nx || y0 == 0 || y0 + TY >= ny);
     const bool xlo = gx == 0, xhi = gx + VX == nx;
-    const bool vecok = gx + VX <= nx;
+    const bool colok = gx < nx;
+    bool rowok[RPT];
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) rowok[rr] = colok && gy0 + rr < ny;
     T* o = dst + (int64_t)z0 * sz + (int64_t)gy0 * sy + gx;
     EnergyAcc<T> eacc;
 
-    // One plane: zm / cz / zp are this thread's values at z-1, z, z+1.
-    auto plane = [&](int z, T (&zm)[RPT][VX], T (&cz)[RPT][VX], T (&zp)[RPT][VX]) {
-        ok = wait_plane(z + 1);
-        read_mine(slot_of(z + 1), zp);
-        const T* cur = slot_of(z);
-        T xi[NP];
-        T below[VX], above[VX];  // rows r0 - 1 and r0 + RPT
-        Vec<T>::get(cur + r0 * BW + VX + xl, below);
-        Vec<T>::get(cur + (r0 + RPT + 1) * BW + VX + xl, above);
+    auto run = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        // One plane: zm / cz / zp are this thread's values at z-1, z, z+1.
+        auto plane = [&](int z, T (&zm)[RPT][VX], T (&cz)[RPT][VX], T (&zp)[RPT][VX]) {
+            const int sn = sc + 1 == S ? 0 : sc + 1;
+            const uint32_t pn = sc + 1 == S ? pc ^ 1u : pc;
+            ok = mbar_wait(&full[sn], pn);
+            read_mine(slot_ptr(sn), zp);
+            const T* cur = slot_ptr(sc);
+            T xi[NP];
+            T below[VX], above[VX];  // rows r0 - 1 and r0 + RPT
+            Vec<T>::get(cur + r0 * BW + VX + xl, below);
+            Vec<T>::get(cur + (r0 + RPT + 1) * BW + VX + xl, above);
 #pragma unroll
-        for (int rr = 0; rr < RPT; ++rr) {
-            const int gyr = gy0 + rr;
-            T ym[VX], yp[VX];
+            for (int rr = 0; rr < RPT; ++rr) {
+                const int gyr = gy0 + rr;
+                T ym[VX], yp[VX];
 #pragma unroll
-            for (int v = 0; v < VX; ++v) {
-                ym[v] = rr == 0 ? below[v] : cz[rr - 1][v];
-                yp[v] = rr == RPT - 1 ? above[v] : cz[rr + 1][v];
-            }
-            // x neighbours across lanes; the tile's outer two come from the halo group
-            T left = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
-            T right = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
-            if (lx == 0) left = cur[(r0 + rr + 1) * BW + VX - 1];
-            if (lx == 31) right = cur[(r0 + rr + 1) * BW + VX + TX];
-            if (edge && gyr < ny) {
-                const int64_t rowoff = (int64_t)z * sz + (int64_t)gyr * sy;
-                if (gyr == 0) {
-                    if (BC == ACS_BC_NEUMANN) {
-#pragma unroll
-                        for (int v = 0; v < VX; ++v) ym[v] = cz[rr][v];
-                    } else if (gx < nx) {
-                        Vec<T>::ldg(src + (int64_t)z * sz + (int64_t)(ny - 1) * sy + gx, ym);
-                    }
+                for (int v = 0; v < VX; ++v) {
+                    ym[v] = rr == 0 ? below[v] : cz[rr - 1][v];
+                    yp[v] = rr == RPT - 1 ? above[v] : cz[rr + 1][v];
                 }
-                if (gyr == ny - 1) {
-                    if (BC == ACS_BC_NEUMANN) {
+                // x neighbours across lanes; the tile's outer two come from the halo
+                // group (every lane reads the same word: a broadcast, no branch)
+                const T hl = cur[(r0 + rr + 1) * BW + VX - 1];
+                const T hr = cur[(r0 + rr + 1) * BW + VX + TX];
+                const T su = __shfl_up_sync(0xffffffffu, cz[rr][VX - 1], 1);
+                const T sd = __shfl_down_sync(0xffffffffu, cz[rr][0], 1);
+                T left = lx == 0 ? hl : su;
+                T right = lx == 31 ? hr : sd;
+                if (EDGE && gyr < ny) {
+                    const int64_t rowoff = (int64_t)z * sz + (int64_t)gyr * sy;
+                    if (gyr == 0) {
+                        if (BC == ACS_BC_NEUMANN) {
 #pragma unroll
-                        for (int v = 0; v < VX; ++v) yp[v] = cz[rr][v];
-                    } else if (gx < nx) {
-                        Vec<T>::ldg(src + (int64_t)z * sz + gx, yp);
-                    }
-                }
-                if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[rowoff + nx - 1];
-                if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[rowoff];
-            }
-            if (MODE == kModeEnergy) {
-                // E_h and max-norm of this (input) state: the forward link of every
-                // unknown along x, y, z (ghost-ruled neighbours as for the step), plus
-                // the links of the first unknowns to the zero Dirichlet boundary
-                if (gyr < ny) {
-#pragma unroll
-                    for (int v = 0; v < VX; ++v) {
-                        if (gx + v >= nx) continue;
-                        const T p = cz[rr][v];
-                        eacc.point(p, v == VX - 1 ? right : cz[rr][v + 1], yp[v], zp[rr][v]);
-                        if (BC == ACS_BC_DIRICHLET) {
-                            if (gx + v == 0) eacc.ghost_link(p);
-                            if (gyr == 0) eacc.ghost_link(p);
-                            if (z == 0) eacc.ghost_link(p);
+                            for (int v = 0; v < VX; ++v) ym[v] = cz[rr][v];
+                        } else if (gx < nx) {
+                            Vec<T>::ldg(src + (int64_t)z * sz + (int64_t)(ny - 1) * sy + gx, ym);
                         }
                     }
+                    if (gyr == ny - 1) {
+                        if (BC == ACS_BC_NEUMANN) {
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) yp[v] = cz[rr][v];
+                        } else if (gx < nx) {
+                            Vec<T>::ldg(src + (int64_t)z * sz + gx, yp);
+                        }
+                    }
+                    if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[rowoff + nx - 1];
+                    if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[rowoff];
                 }
-                continue;
-            }
+                if (MODE == kModeEnergy) {
+                    // E_h and max-norm of this (input) state: the forward link of every
+                    // unknown along x, y, z (ghost-ruled neighbours as for the step), plus
+                    // the links of the first unknowns to the zero Dirichlet boundary
+                    if (gyr < ny) {
 #pragma unroll
-            for (int v = 0; v < VX; ++v) {
-                const T xm = v == 0 ? left : cz[rr][v - 1];
-                const T xp = v == VX - 1 ? right : cz[rr][v + 1];
-                const T s = nsum(zm[rr][v], zp[rr][v], ym[v], yp[v], xm, xp);
-                xi[rr * VX + v] = predictor(cz[rr][v], s, c);
-            }
-        }
-        if (MODE == kModeEnergy) {
-            eacc.plane_done();
-            failed = __syncthreads_or(!ok);
-            if (!failed && tid == 0 && z + S <= z1) issue(z + S);
-            if (!failed) last_issued = max(last_issued, min(z + S, z1));
-            return;
-        }
-        T out[NP];
-        roots<T, SOLVE, NP>(xi, out, c);
+                        for (int v = 0; v < VX; ++v) {
+                            if (gx + v >= nx) continue;
+                            const T p = cz[rr][v];
+                            eacc.point(p, v == VX - 1 ? right : cz[rr][v + 1], yp[v], zp[rr][v]);
+                            if (BC == ACS_BC_DIRICHLET) {
+                                if (gx + v == 0) eacc.ghost_link(p);
+                                if (gyr == 0) eacc.ghost_link(p);
+                                if (z == 0) eacc.ghost_link(p);
+                            }
+                        }
+                    }
+                    continue;
+                }
 #pragma unroll
-        for (int rr = 0; rr < RPT; ++rr) {
-            if (gy0 + rr >= ny) continue;
-            if (vecok) {
-                Vec<T>::put(o + rr * sy, &out[rr * VX]);
+                for (int v = 0; v < VX; ++v) {
+                    const T xm = v == 0 ? left : cz[rr][v - 1];
+                    const T xp = v == VX - 1 ? right : cz[rr][v + 1];
+                    const T s = nsum(zm[rr][v], zp[rr][v], ym[v], yp[v], xm, xp);
+                    xi[rr * VX + v] = predictor(cz[rr][v], s, c);
+                }
+            }
+            if (MODE == kModeEnergy) {
+                eacc.plane_done();
             } else {
+                T out[NP];
+                roots<T, SOLVE, NP>(xi, out, c);
 #pragma unroll
-                for (int v = 0; v < VX; ++v)
-                    if (gx + v < nx) o[rr * sy + v] = out[rr * VX + v];
+                for (int rr = 0; rr < RPT; ++rr)
+                    if (rowok[rr]) Vec<T>::put(o + rr * sy, &out[rr * VX]);
+                o += sz;
             }
-        }
-        o += sz;
-        failed = __syncthreads_or(!ok);
-        if (!failed && tid == 0 && z + S <= z1) issue(z + S);
-        if (!failed) last_issued = max(last_issued, min(z + S, z1));
-    };
+            failed = __syncthreads_or(!ok);
+            // plane z + S reuses plane z's slot, free now that every thread is past it
+            if (!failed && tid == 0 && z + S <= z1) issue(z + S, sc);
+            if (!failed) last_issued = max(last_issued, min(z + S, z1));
+            sc = sn;
+            pc = pn;
+        };
 
-    // the three register sets rotate roles, so the loop is unrolled by three
-    T zq[RPT][VX];
-    int z = z0;
-    for (; z + 3 <= z1 && !failed; z += 3) {
-        plane(z, zm, cz, zq);
-        if (failed) break;
-        plane(z + 1, cz, zq, zm);
-        if (failed) break;
-        plane(z + 2, zq, zm, cz);
-    }
-    if (!failed && z < z1) {
-        plane(z, zm, cz, zq);
-        if (!failed && z + 1 < z1) plane(z + 1, cz, zq, zm);
-    }
+        // the three register sets rotate roles, so the loop is unrolled by three
+        T zq[RPT][VX];
+        int z = z0;
+        for (; z + 3 <= z1 && !failed; z += 3) {
+            plane(z, zm, cz, zq);
+            if (failed) break;
+            plane(z + 1, cz, zq, zm);
+            if (failed) break;
+            plane(z + 2, zq, zm, cz);
+        }
+        if (!failed && z < z1) {
+            plane(z, zm, cz, zq);
+            if (!failed && z + 1 < z1) plane(z + 1, cz, zq, zm);
+        }
+    };
+    if (edge) run(std::true_type());
+    else run(std::false_type());
+
     if (MODE == kModeEnergy) energy_block_write(eacc, part + (blockIdx.y * gridDim.x + blockIdx.x));
     if (failed) {
         // record the timeout, then let the newest load of every slot land (bounded)
