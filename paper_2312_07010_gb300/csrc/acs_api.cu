@@ -232,6 +232,7 @@ size_t work_total(const acs_ctx* c) { return off_flags(c) + kAlign; }
 void drop_graphs(acs_ctx* c) {
     for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
     c->graphs.clear();
+    grad_drop_graphs(c->grad);
 }
 
 void refresh_coef(acs_ctx* c) {
@@ -393,7 +394,7 @@ CtxView ctx_view(acs_ctx* c) {
     CtxView v;
     v.dims = c->dims; v.bc = c->bc; v.dtype = c->dtype; v.g = c->g; v.esize = c->esize;
     v.lam = c->lam; v.dt = c->dt; v.h = c->h; v.eps = c->eps;
-    v.phi = c->phi; v.other = c->other; v.stream = c->stream; v.partials = c->partials;
+    v.phi = c->phi; v.other = c->other; v.stream = c->stream; v.cap = c->cap; v.err = c->err; v.partials = c->partials;
     v.result = c->result; v.steps_done = c->steps_done; v.cf = c->cf; v.cd = c->cd; v.grad = &c->grad;
     return v;
 }

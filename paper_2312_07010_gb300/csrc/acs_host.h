@@ -5,12 +5,21 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "acs_kernels.cuh"
 
 namespace acs {
 
 // Adjoint recording state of a context (see acs_grad_bind in acs.h).
+// A recorded CUDA graph of the adjoint unit: kind 0 = recording forward (a = first
+// step, b = steps), kind 1 = backward sweep (a = recorded steps, b = checkpoint spacing).
+struct GradGraph {
+    int kind;
+    int64_t a, b;
+    cudaGraphExec_t exec;
+};
+
 struct GradState {
     bool active = false;
     char* buf = nullptr;
@@ -18,7 +27,12 @@ struct GradState {
     int64_t max_steps = 0, every = 1;
     int64_t recorded = 0;  // steps recorded since the last set_state
     bool started = false;  // checkpoint 0 holds phi^0
+    std::vector<GradGraph> graphs;
 };
+
+// Release the adjoint unit's recorded graphs (their kernels bake in pointers and
+// coefficients, so any change of those invalidates them).
+void grad_drop_graphs(GradState& G);
 
 // What the other translation units may see of a context.
 struct CtxView {
@@ -29,6 +43,8 @@ struct CtxView {
     void* phi;
     void* other;
     cudaStream_t stream;
+    cudaStream_t cap;  // stream used for graph capture
+    int* err;          // device flag set by kernels whose bounded waits gave up
     RedPartial* partials;
     double* result;
     int64_t steps_done;

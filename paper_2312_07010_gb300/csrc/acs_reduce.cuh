@@ -34,15 +34,17 @@ __device__ __forceinline__ CSum shfl_down(CSum v, int off) {
     return CSum{__shfl_down_sync(0xffffffffu, v.s, off), __shfl_down_sync(0xffffffffu, v.c, off)};
 }
 
-// Sum a CSum over a block of blockDim.x threads (<= 1024) in a fixed order; the
+// Sum a CSum over the threads of a block (<= 1024, any shape) in a fixed order; the
 // result is valid in thread 0.  `scratch` needs 32 entries.
 __device__ __forceinline__ CSum block_csum(CSum v, CSum* scratch) {
     for (int off = 16; off > 0; off >>= 1) v = cmerge(v, shfl_down(v, off));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) scratch[warp] = v;
+    // linear thread index, so 2D blocks (32 x k) reduce correctly too
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nwarps = (int)((blockDim.x * blockDim.y + 31) >> 5);
+    if ((tid & 31) == 0) scratch[tid >> 5] = v;
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w) v = cmerge(v, scratch[w]);
+    if (tid == 0)
+        for (int w = 1; w < nwarps; ++w) v = cmerge(v, scratch[w]);
     return v;
 }
 

@@ -20,7 +20,9 @@
 
 #include "acs_host.h"
 #include "acs_reduce.cuh"
+#include "stream_tile.cuh"
 #include "tile2d.cuh"
+#include "tma.cuh"
 
 namespace acs {
 
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const T* __restrict__ phin, con
     }
     __shared__ CSum scratch[32];
     ge = block_csum(ge, scratch);
-    if (threadIdx.x == 0) part[blockIdx.x] = ge;
+    if (threadIdx.x == 0) part[blockIdx.x] = cmerge(part[blockIdx.x], ge);
 }
 
 // acc += the partials of a segment: steps x nparts entries, in a fixed order.
@@ -186,14 +188,229 @@ __global__ void __launch_bounds__(256) k_adjoint2d(const T* __restrict__ phin, c
     }
     __shared__ CSum scratch[32];
     ge = block_csum(ge, scratch);
-    if (threadIdx.x == 0) part[blockIdx.x] = ge;
+    if (threadIdx.x == 0) part[blockIdx.x] = cmerge(part[blockIdx.x], ge);
 }
 
-// One adjoint step writing its per-block eps^2 partials to `part` (kMaxRedBlocks
-// entries); returns the number of partials used in *nparts.
+// 2D adjoint step streamed through TMA (rows a multiple of 16 bytes).  A CTA owns a
+// column of TX unknowns and a run of 16-row blocks; per block one thread loads the
+// halo boxes of phi^n, phi^{n+1} and adj^{n+1} into a ring slot.  mu is formed in
+// place over the adj^{n+1} box (zero outside the grid, which is the Dirichlet
+// ghost), then each thread updates its RPT x VX points with mu and phi^n neighbours
+// from registers, shuffles and shared memory; at a Neumann face the ghost is the
+// point itself, at a periodic face the wrapped value, read from global memory.
+template <typename T, int BC, bool EDGE>
+__device__ __forceinline__ void adjoint_block(const T* P, const T* M, const T* __restrict__ phin,
+                                              const T* __restrict__ phin1, const T* __restrict__ adj1,
+                                              T* __restrict__ adj0, const Geo& g, const Coef<T>& cf, int x0, int y0,
+                                              T& tile_sum) {
+    using TT = Tile3<T, 2, 2>;
+    constexpr int VX = TT::VX, TX = TT::TX, BW = TT::BW, RPT = TT::RPT;
+    const int nx = (int)g.nx, ny = (int)g.ny;
+    const int64_t sy = g.sy;
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int xl = lx * VX, gx = x0 + xl, r0 = RPT * ly, gy0 = y0 + r0;
+    auto mu_at = [&](int64_t j) {
+        const T t = phin1[j];
+        return adj1[j] / dfma(cf.three_a, t * t, cf.b);
+    };
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+        const int br = r0 + rr + 1;  // box row of grid row gyr
+        const int gyr = gy0 + rr;
+        T mu[VX], p[VX], mb[VX], ma[VX], pb[VX], pa[VX];
+        Vec<T>::get(M + br * BW + VX + xl, mu);
+        Vec<T>::get(P + br * BW + VX + xl, p);
+        Vec<T>::get(M + (br - 1) * BW + VX + xl, mb);
+        Vec<T>::get(M + (br + 1) * BW + VX + xl, ma);
+        Vec<T>::get(P + (br - 1) * BW + VX + xl, pb);
+        Vec<T>::get(P + (br + 1) * BW + VX + xl, pa);
+        // the tile's outer two x neighbours from the halo group (a broadcast read)
+        const T mhl = M[br * BW + VX - 1], mhr = M[br * BW + VX + TX];
+        const T phl = P[br * BW + VX - 1], phr = P[br * BW + VX + TX];
+        const T msu = __shfl_up_sync(0xffffffffu, mu[VX - 1], 1), msd = __shfl_down_sync(0xffffffffu, mu[0], 1);
+        const T psu = __shfl_up_sync(0xffffffffu, p[VX - 1], 1), psd = __shfl_down_sync(0xffffffffu, p[0], 1);
+        T ml = lx == 0 ? mhl : msu, mr = lx == 31 ? mhr : msd;
+        T pl = lx == 0 ? phl : psu, pr = lx == 31 ? phr : psd;
+        if (EDGE && gyr < ny && gx < nx) {
+            if (gyr == 0) {
+                if (BC == ACS_BC_NEUMANN) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) { mb[v] = mu[v]; pb[v] = p[v]; }
+                } else if (BC == ACS_BC_PERIODIC) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        const int64_t j = (int64_t)(ny - 1) * sy + gx + v;
+                        mb[v] = mu_at(j);
+                        pb[v] = phin[j];
+                    }
+                }
+            }
+            if (gyr == ny - 1) {
+                if (BC == ACS_BC_NEUMANN) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) { ma[v] = mu[v]; pa[v] = p[v]; }
+                } else if (BC == ACS_BC_PERIODIC) {
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        const int64_t j = gx + v;
+                        ma[v] = mu_at(j);
+                        pa[v] = phin[j];
+                    }
+                }
+            }
+            if (gx == 0) {
+                if (BC == ACS_BC_NEUMANN) {
+                    ml = mu[0];
+                    pl = p[0];
+                } else if (BC == ACS_BC_PERIODIC) {
+                    const int64_t j = (int64_t)gyr * sy + nx - 1;
+                    ml = mu_at(j);
+                    pl = phin[j];
+                }
+            }
+            if (gx + VX == nx) {
+                if (BC == ACS_BC_NEUMANN) {
+                    mr = mu[VX - 1];
+                    pr = p[VX - 1];
+                } else if (BC == ACS_BC_PERIODIC) {
+                    const int64_t j = (int64_t)gyr * sy;
+                    mr = mu_at(j);
+                    pr = phin[j];
+                }
+            }
+        }
+        T out[VX];
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+            const T mxm = v == 0 ? ml : mu[v - 1], mxp = v == VX - 1 ? mr : mu[v + 1];
+            const T pxm = v == 0 ? pl : p[v - 1], pxp = v == VX - 1 ? pr : p[v + 1];
+            const T smu = nsum(mb[v], ma[v], mxm, mxp);
+            const T sphi = nsum(pb[v], pa[v], pxm, pxp);
+            out[v] = dfma(cf.lam, smu, mu[v] * dfma(-cf.three_a, p[v] * p[v], cf.c0));
+            if (gyr < ny && gx + v < nx) tile_sum = dfma(mu[v], sphi - T(4) * p[v], tile_sum);
+        }
+        if (gyr < ny && gx < nx) Vec<T>::put(adj0 + (int64_t)gyr * sy + gx, out);
+    }
+}
+
+template <typename T, int BC>
+__global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ CUtensorMap map_p,
+                                                       const __grid_constant__ CUtensorMap map_q,
+                                                       const __grid_constant__ CUtensorMap map_l,
+                                                       const T* __restrict__ phin, const T* __restrict__ phin1,
+                                                       const T* __restrict__ adj1, T* __restrict__ adj0, Geo g,
+                                                       Coef<T> cf, int ybchunk, int* err, CSum* part) {
+    using TT = Tile3<T, 2, 2>;
+    constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, S = TT::S;
+    constexpr int BOX = TT::SLOT_STRIDE / sizeof(T);  // elements per box (128-byte aligned)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base);
+    T* ring = reinterpret_cast<T*>(base + TT::BAR_BYTES);  // S slots of 3 boxes: phi^n, phi^{n+1}, adj^{n+1}
+    const int nx = (int)g.nx, ny = (int)g.ny;
+    const int nyb = (ny + TY - 1) / TY;
+    const int x0 = blockIdx.x * TX;
+    const int b0 = blockIdx.y * ybchunk, b1 = min(b0 + ybchunk, nyb);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int b, int slot) {
+        T* d = ring + (size_t)slot * 3 * BOX;
+        if ((smem_u32(d) & 127u) != 0u || (((x0 - VX) * (int)sizeof(T)) & 15) != 0) {
+            atomicExch(err, 2);
+            return;
+        }
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[slot], 3u * TT::SLOT_BYTES);
+        tma_load_2d(d, &map_p, &full[slot], x0 - VX, b * TY - 1);
+        tma_load_2d(d + BOX, &map_q, &full[slot], x0 - VX, b * TY - 1);
+        tma_load_2d(d + 2 * BOX, &map_l, &full[slot], x0 - VX, b * TY - 1);
+    };
+    int last_issued = min(b0 + S, b1) - 1;
+    if (tid == 0)
+        for (int b = b0; b <= last_issued; ++b) issue(b, b - b0);
+    const bool edge = BC != ACS_BC_DIRICHLET && (x0 == 0 || x0 + TX >= nx || b0 == 0 || b1 * TY >= ny);
+    CSum ge{0.0, 0.0};
+    bool failed = false;
+    int sc = 0;
+    uint32_t pc = 0u;
+    for (int b = b0; b < b1 && !failed; ++b) {
+        const bool ok = mbar_wait(&full[sc], pc);
+        T* P = ring + (size_t)sc * 3 * BOX;
+        const T* Q = P + BOX;
+        T* M = P + 2 * BOX;
+        // mu over the whole box, in place of adj^{n+1}
+        for (int i = tid; i < TT::SLOT; i += 256) {
+            const T q = Q[i];
+            M[i] = M[i] / dfma(cf.three_a, q * q, cf.b);
+        }
+        __syncthreads();
+        T tile_sum = T(0);
+        if (edge && (x0 == 0 || x0 + TX >= nx || b == 0 || (b + 1) * TY >= ny))
+            adjoint_block<T, BC, true>(P, M, phin, phin1, adj1, adj0, g, cf, x0, b * TY, tile_sum);
+        else
+            adjoint_block<T, BC, false>(P, M, phin, phin1, adj1, adj0, g, cf, x0, b * TY, tile_sum);
+        cadd(ge, (double)tile_sum);
+        failed = __syncthreads_or(!ok);
+        // block b + S reuses block b's slot, free now that every thread is past it
+        if (!failed && tid == 0 && b + S < b1) {
+            issue(b + S, sc);
+            last_issued = b + S;
+        }
+        if (++sc == S) {
+            sc = 0;
+            pc ^= 1u;
+        }
+    }
+    if (failed && tid == 0) {
+        atomicExch(err, 1);
+        for (int b = max(b0, last_issued - S + 1); b <= last_issued; ++b) {
+            const int k = b - b0;
+            mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
+        }
+    }
+    __shared__ CSum scratch[32];
+    ge = block_csum(ge, scratch);
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    if (tid == 0) part[cta] = cmerge(part[cta], ge);
+}
+
+// One adjoint step adding its per-block eps^2 partials into `part` (kMaxRedBlocks
+// entries, the same CTA -> entry map every step); returns their number in *nparts.
 template <typename T>
 static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin1, const T* adj1, T* adj0,
-                                  const Geo& g, const Coef<T>& cf, CSum* part, int* nparts, cudaStream_t st) {
+                                  const Geo& g, const Coef<T>& cf, CSum* part, int* nparts, int* err,
+                                  cudaStream_t st) {
+    if (dims == 2 && (g.nx * (int64_t)sizeof(T)) % 16 == 0 && g.nx < (1 << 30) && g.ny < (1 << 30) && err) {
+        using TT = Tile3<T, 2, 2>;
+        const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX), nyb = (int)((g.ny + TT::TY - 1) / TT::TY);
+        // about three CTAs per SM, at most kMaxRedBlocks partials
+        const int want = std::max(1, std::min(kMaxRedBlocks, 152 * 3) / ntx);
+        const int chunks = std::max(1, std::min(nyb, want));
+        const int ybchunk = (nyb + chunks - 1) / chunks;
+        const int nchunks = (nyb + ybchunk - 1) / ybchunk;
+        if ((int64_t)ntx * nchunks <= kMaxRedBlocks && nchunks <= 65535) {
+            CUtensorMap mp, mq, ml;
+            const uint64_t dims2[2] = {(uint64_t)g.nx, (uint64_t)g.ny};
+            const uint32_t box[2] = {(uint32_t)TT::BW, (uint32_t)TT::BH};
+            if (encode_tensor_map(&mp, sizeof(T), 2, phin, dims2, box) &&
+                encode_tensor_map(&mq, sizeof(T), 2, phin1, dims2, box) &&
+                encode_tensor_map(&ml, sizeof(T), 2, adj1, dims2, box)) {
+                const size_t smem = 128 + TT::BAR_BYTES + (size_t)TT::S * 3 * TT::SLOT_STRIDE;
+                auto kern =
+                    bc == 0 ? k_adjoint2d_tma<T, 0> : (bc == 1 ? k_adjoint2d_tma<T, 1> : k_adjoint2d_tma<T, 2>);
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                kern<<<dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), smem, st>>>(
+                    mp, mq, ml, phin, phin1, adj1, adj0, g, cf, ybchunk, err, part);
+                *nparts = ntx * nchunks;
+                return cudaGetLastError();
+            }
+        }
+    }
     if (dims == 2 && g.nx < (1 << 30) && g.ny < (1 << 30)) {
         using TT = Tile2<T>;
         const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX), nty = (int)((g.ny + TT::TY - 1) / TT::TY);
@@ -261,25 +478,70 @@ int grad_on_set_state(acs_ctx* c) {
     return ACS_OK;
 }
 
+void grad_drop_graphs(GradState& G) {
+    for (auto& g : G.graphs) cudaGraphExecDestroy(g.exec);
+    G.graphs.clear();
+}
+
+// Record one graph of `enqueue(stream)` on the capture stream and cache it under
+// (kind, a, b); null if the stream cannot be captured (the caller then runs directly).
+template <typename F>
+static cudaGraphExec_t grad_graph(const CtxView& v, int kind, int64_t a, int64_t b, F&& enqueue) {
+    GradState& G = *v.grad;
+    for (auto& g : G.graphs)
+        if (g.kind == kind && g.a == a && g.b == b) return g.exec;
+    if (!v.cap) return nullptr;
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(v.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+    const bool ok = enqueue(v.cap);
+    const cudaError_t e2 = cudaStreamEndCapture(v.cap, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (!ok || e2 != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+    if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+    if (!exec) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (G.graphs.size() >= 8) {
+        cudaGraphExecDestroy(G.graphs.front().exec);
+        G.graphs.erase(G.graphs.begin());
+    }
+    G.graphs.push_back(GradGraph{kind, a, b, exec});
+    return exec;
+}
+
+// n steps from the current state with a checkpoint copy at every multiple of `every`
+// (one recorded graph per (first step, n)).
 int grad_record_steps(acs_ctx* c, int64_t n) {
     CtxView v = ctx_view(c);
     GradState& G = *v.grad;
     if (!G.started) return ACS_E_STATE;
     if (G.recorded + n > G.max_steps) return ACS_E_NOMEM;
-    GradLayout L = layout(v, G.max_steps, G.every);
-    while (n > 0) {
-        const int64_t room = G.every - (G.recorded % G.every);
-        const int64_t k = std::min(n, room);
-        if (ctx_enqueue_steps(c, k, v.stream) != cudaSuccess) return ACS_E_CUDA;
-        G.recorded += k;
-        n -= k;
-        if (G.recorded % G.every == 0) {
-            char* slot = G.buf + L.ckpt + L.sb * (size_t)(G.recorded / G.every);
-            if (cudaMemcpyAsync(slot, v.phi, (size_t)v.g.total * v.esize, cudaMemcpyDeviceToDevice, v.stream) !=
-                cudaSuccess)
-                return ACS_E_CUDA;
+    const GradLayout L = layout(v, G.max_steps, G.every);
+    const int64_t start = G.recorded;
+    auto enqueue = [&](cudaStream_t st) -> bool {
+        int64_t rec = start, left = n;
+        while (left > 0) {
+            const int64_t k = std::min(left, G.every - (rec % G.every));
+            if (ctx_enqueue_steps(c, k, st) != cudaSuccess) return false;
+            rec += k;
+            left -= k;
+            if (rec % G.every == 0) {
+                char* slot = G.buf + L.ckpt + L.sb * (size_t)(rec / G.every);
+                if (cudaMemcpyAsync(slot, v.phi, (size_t)v.g.total * v.esize, cudaMemcpyDeviceToDevice, st) !=
+                    cudaSuccess)
+                    return false;
+            }
         }
+        return true;
+    };
+    cudaGraphExec_t exec = n >= 4 ? grad_graph(v, 0, start, n, enqueue) : nullptr;
+    if (exec) {
+        if (cudaGraphLaunch(exec, v.stream) != cudaSuccess) return ACS_E_CUDA;
+    } else if (!enqueue(v.stream)) {
+        return ACS_E_CUDA;
     }
+    G.recorded += n;
     return ACS_OK;
 }
 
@@ -302,6 +564,7 @@ ACS_API int acs_grad_bind(acs_ctx* c, void* d_grad_work, size_t bytes, int64_t m
     GradLayout L = layout(v, max_steps, every);
     if (bytes < L.total) return ACS_E_NOMEM;
     GradState& G = *v.grad;
+    grad_drop_graphs(G);
     G.active = true;
     G.buf = (char*)d_grad_work;
     G.bytes = bytes;
@@ -327,44 +590,65 @@ ACS_API int acs_grad(acs_ctx* c, const void* d_dL_dphiT, void* d_dL_dphi0, doubl
     CSum* part = (CSum*)(G.buf + L.part);
     CSum* acc = (CSum*)(G.buf + L.acc);
     if (cudaMemcpyAsync(A, d_dL_dphiT, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return ACS_E_CUDA;
-    k_zero_acc<<<1, 1, 0, st>>>(acc);
     const int64_t N = G.recorded;
-    if (N > 0) {
-        for (int64_t seg = (N - 1) / G.every; seg >= 0; --seg) {
+    // The whole sweep, recorded once per (N, every): per segment (last first)
+    // recompute its states from the checkpoint, then step the adjoint back through
+    // them.  Each adjoint launch adds its per-CTA eps^2 partials into part[cta]
+    // (always the same CTA order), folded once at the end: deterministic.
+    auto sweep = [&](cudaStream_t s) -> bool {
+        char* a = A;
+        char* b = B;
+        k_zero_acc<<<1, 1, 0, s>>>(acc);
+        if (cudaMemsetAsync(part, 0, sizeof(CSum) * kMaxRedBlocks, s) != cudaSuccess) return false;
+        int nparts = 0;
+        for (int64_t seg = N > 0 ? (N - 1) / G.every : -1; seg >= 0; --seg) {
             const int64_t s0 = seg * G.every;
             const int64_t m = std::min(G.every, N - s0);
             char* ck = G.buf + L.ckpt + L.sb * (size_t)seg;
-            // recompute phi^{s0+1} .. phi^{s0+m} into the segment buffer
             const char* prev = ck;
             for (int64_t j = 0; j < m; ++j) {
                 char* dst = G.buf + L.seg + L.sb * (size_t)j;
-                if (ctx_launch_one(c, prev, dst, st) != cudaSuccess) return ACS_E_CUDA;
+                if (ctx_launch_one(c, prev, dst, s) != cudaSuccess) return false;
                 prev = dst;
             }
-            int nparts = 0;
             for (int64_t k = m - 1; k >= 0; --k) {
                 const char* pk = k == 0 ? ck : G.buf + L.seg + L.sb * (size_t)(k - 1);
                 const char* pk1 = G.buf + L.seg + L.sb * (size_t)k;
-                CSum* pst = part + (size_t)(m - 1 - k) * kMaxRedBlocks;
                 cudaError_t e;
                 if (v.dtype == ACS_F32)
-                    e = launch_adjoint<float>(v.dims, v.bc, (const float*)pk, (const float*)pk1, (const float*)A,
-                                              (float*)B, v.g, v.cf, pst, &nparts, st);
+                    e = launch_adjoint<float>(v.dims, v.bc, (const float*)pk, (const float*)pk1, (const float*)a,
+                                              (float*)b, v.g, v.cf, part, &nparts, v.err, s);
                 else
                     e = launch_adjoint<double>(v.dims, v.bc, (const double*)pk, (const double*)pk1,
-                                               (const double*)A, (double*)B, v.g, v.cd, pst, &nparts, st);
-                if (e != cudaSuccess) return ACS_E_CUDA;
-                std::swap(A, B);
+                                               (const double*)a, (double*)b, v.g, v.cd, part, &nparts, v.err, s);
+                if (e != cudaSuccess) return false;
+                std::swap(a, b);
             }
-            // the segment's eps^2 partials, in a fixed order
-            k_adjoint_finish<<<1, 256, 0, st>>>(part, (int)m, kMaxRedBlocks, nparts, acc);
-            if (cudaGetLastError() != cudaSuccess) return ACS_E_CUDA;
         }
+        if (nparts > 0) {
+            k_adjoint_finish<<<1, 256, 0, s>>>(part, 1, kMaxRedBlocks, nparts, acc);
+            if (cudaGetLastError() != cudaSuccess) return false;
+        }
+        return true;
+    };
+    cudaGraphExec_t exec = N >= 4 ? grad_graph(v, 1, N, G.every, sweep) : nullptr;
+    if (exec) {
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) return ACS_E_CUDA;
+    } else if (!sweep(st)) {
+        return ACS_E_CUDA;
     }
+    // after N adjoint steps the result is in A for even N, in B for odd N
+    if (N & 1) std::swap(A, B);
     if (cudaMemcpyAsync(d_dL_dphi0, A, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return ACS_E_CUDA;
     CSum h;
     if (cudaMemcpyAsync(&h, acc, sizeof(CSum), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ACS_E_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return ACS_E_CUDA;
+    int flag = 0;
+    if (v.err && cudaMemcpy(&flag, v.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_E_CUDA;
+    if (flag) {
+        cudaMemset(v.err, 0, sizeof(int));
+        return ACS_E_TIMEOUT;
+    }
     *dL_deps2_host = (h.s + h.c) * (v.dt / (v.h * v.h));
     return std::isfinite(*dL_deps2_host) ? ACS_OK : ACS_E_NONFINITE;
 }
