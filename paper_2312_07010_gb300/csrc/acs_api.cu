@@ -730,6 +730,11 @@ ACS_API int acs_autotune(acs_ctx* c, double* us_per_step) {
                 cands.push_back({ACS_KERNEL_TILED, 1, v, 16});
                 cands.push_back({ACS_KERNEL_TILED, 1, v, 32});
             }
+            if (c->dims == 2) {
+                // 16-row blocks per CTA
+                cands.push_back({ACS_KERNEL_TILED, 1, v, 1});
+                cands.push_back({ACS_KERNEL_TILED, 1, v, 2});
+            }
         }
     }
     for (int k = 2; k <= 8; ++k)

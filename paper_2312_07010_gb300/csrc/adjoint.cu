@@ -191,6 +191,34 @@ __global__ void __launch_bounds__(256) k_adjoint2d(const T* __restrict__ phin, c
     if (threadIdx.x == 0) part[blockIdx.x] = cmerge(part[blockIdx.x], ge);
 }
 
+// mu = adj / (3 a theta^2 + b) of the streamed kernel: the denominator lies in
+// [b, 1 + 2a], well away from 0, so a reciprocal suffices -- FP32: the fast
+// division (2 ulp); FP64: the FP32 reciprocal refined by two Newton steps.
+__device__ __forceinline__ float adj_mu(float l, float q, const Coef<float>& cf) {
+    return __fdividef(l, __fmaf_rn(cf.three_a, q * q, cf.b));
+}
+__device__ __forceinline__ double adj_mu(double l, double q, const Coef<double>& cf) {
+    const double d = __fma_rn(cf.three_a, q * q, cf.b);
+    double r = (double)__frcp_rn((float)d);
+    r = r * __fma_rn(-d, r, 2.0);
+    r = r * __fma_rn(-d, r, 2.0);
+    return l * r;
+}
+
+// Sum of one value per thread over a block of 32 x 8 threads: warp shuffles in T,
+// the eight warp sums folded in FP64 by thread (0, 0), where the result is valid.
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v) {
+    __shared__ T ws[8];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) ws[threadIdx.y] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int w = 0; w < 8; ++w) t += (double)ws[w];
+    return t;
+}
+
 // 2D adjoint step streamed through TMA (rows a multiple of 16 bytes).  A CTA owns a
 // column of TX unknowns and a run of 16-row blocks; per block one thread loads the
 // halo boxes of phi^n, phi^{n+1} and adj^{n+1} into a ring slot.  mu is formed in
@@ -209,10 +237,7 @@ __device__ __forceinline__ void adjoint_block(const T* P, const T* M, const T* _
     const int64_t sy = g.sy;
     const int lx = threadIdx.x, ly = threadIdx.y;
     const int xl = lx * VX, gx = x0 + xl, r0 = RPT * ly, gy0 = y0 + r0;
-    auto mu_at = [&](int64_t j) {
-        const T t = phin1[j];
-        return adj1[j] / dfma(cf.three_a, t * t, cf.b);
-    };
+    auto mu_at = [&](int64_t j) { return adj_mu(adj1[j], phin1[j], cf); };
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
         const int br = r0 + rr + 1;  // box row of grid row gyr
@@ -333,7 +358,7 @@ __global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ C
     if (tid == 0)
         for (int b = b0; b <= last_issued; ++b) issue(b, b - b0);
     const bool edge = BC != ACS_BC_DIRICHLET && (x0 == 0 || x0 + TX >= nx || b0 == 0 || b1 * TY >= ny);
-    CSum ge{0.0, 0.0};
+    T tile_sum = T(0);  // this thread's eps^2 terms of the launch
     bool failed = false;
     int sc = 0;
     uint32_t pc = 0u;
@@ -343,17 +368,12 @@ __global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ C
         const T* Q = P + BOX;
         T* M = P + 2 * BOX;
         // mu over the whole box, in place of adj^{n+1}
-        for (int i = tid; i < TT::SLOT; i += 256) {
-            const T q = Q[i];
-            M[i] = M[i] / dfma(cf.three_a, q * q, cf.b);
-        }
+        for (int i = tid; i < TT::SLOT; i += 256) M[i] = adj_mu(M[i], Q[i], cf);
         __syncthreads();
-        T tile_sum = T(0);
         if (edge && (x0 == 0 || x0 + TX >= nx || b == 0 || (b + 1) * TY >= ny))
             adjoint_block<T, BC, true>(P, M, phin, phin1, adj1, adj0, g, cf, x0, b * TY, tile_sum);
         else
             adjoint_block<T, BC, false>(P, M, phin, phin1, adj1, adj0, g, cf, x0, b * TY, tile_sum);
-        cadd(ge, (double)tile_sum);
         failed = __syncthreads_or(!ok);
         // block b + S reuses block b's slot, free now that every thread is past it
         if (!failed && tid == 0 && b + S < b1) {
@@ -372,10 +392,14 @@ __global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ C
             mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
         }
     }
-    __shared__ CSum scratch[32];
-    ge = block_csum(ge, scratch);
+    // the CTA's share of the step, added to its FP64 running sum over the sweep
+    const double t = block_sum_t<T>(tile_sum);
     const int cta = blockIdx.y * gridDim.x + blockIdx.x;
-    if (tid == 0) part[cta] = cmerge(part[cta], ge);
+    if (tid == 0) {
+        CSum ge{0.0, 0.0};
+        cadd(ge, t);
+        part[cta] = cmerge(part[cta], ge);
+    }
 }
 
 // One adjoint step adding its per-block eps^2 partials into `part` (kMaxRedBlocks
@@ -388,7 +412,8 @@ static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin
         using TT = Tile3<T, 2, 2>;
         const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX), nyb = (int)((g.ny + TT::TY - 1) / TT::TY);
         // about three CTAs per SM, at most kMaxRedBlocks partials
-        const int want = std::max(1, std::min(kMaxRedBlocks, 152 * 3) / ntx);
+        // one block per CTA while the partials fit, else about three CTAs per SM
+        const int want = (int64_t)ntx * nyb <= kMaxRedBlocks ? nyb : std::max(1, (152 * 3) / ntx);
         const int chunks = std::max(1, std::min(nyb, want));
         const int ybchunk = (nyb + chunks - 1) / chunks;
         const int nchunks = (nyb + ybchunk - 1) / ybchunk;

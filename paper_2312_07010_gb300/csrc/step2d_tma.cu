@@ -197,10 +197,15 @@ static cudaError_t launch2d_variant(int bc, const T* src, T* dst, const Geo& g, 
     const int ntx = (int)((g.nx + TT::TX - 1) / TT::TX);
     const int nyb = (int)((g.ny + TT::TY - 1) / TT::TY);
     if (ybchunk <= 0) {
-        // about eight CTAs per SM over the launch, at least four blocks each
-        const int want = 152 * 8;
-        const int chunks = std::max(1, std::min(nyb / 4 > 0 ? nyb / 4 : 1, (want + ntx - 1) / ntx));
-        ybchunk = (nyb + chunks - 1) / chunks;
+        if ((int64_t)ntx * nyb <= 152 * 6) {
+            // a small grid: one block per CTA, as many CTAs as there are blocks
+            ybchunk = 1;
+        } else {
+            // about eight CTAs per SM over the launch, at least four blocks each
+            const int want = 152 * 8;
+            const int chunks = std::max(1, std::min(nyb / 4 > 0 ? nyb / 4 : 1, (want + ntx - 1) / ntx));
+            ybchunk = (nyb + chunks - 1) / chunks;
+        }
     }
     const int nchunks = (nyb + ybchunk - 1) / ybchunk;
     if (nchunks > 65535) return cudaErrorNotSupported;
