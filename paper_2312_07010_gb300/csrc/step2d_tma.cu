@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_s
             }
         }
     };
-    if (edge) run(std::true_type());
+    // the reduction's long loop body is kept in one copy (the fix-ups test their own
+    // rows), so the instruction cache holds it; the step runs a lean copy off the faces
+    if ((MODE == kModeEnergy && BC != ACS_BC_DIRICHLET) || edge) run(std::true_type());
     else run(std::false_type());
     if (MODE == kModeEnergy) energy_block_write(eacc, part + (blockIdx.y * gridDim.x + blockIdx.x));
     if (failed) {
