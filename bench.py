@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--depth", type=int, default=1)
     ap.add_argument("--profile", action="store_true",
                     help="only set up the 512^3 workload and run --steps time steps (for ncu captures)")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="only run --steps forward+backward passes of the 1024^2 adjoint workload")
     ap.add_argument("--profile-batch", action="store_true",
                     help="only set up the 256-instance batched workload and run --steps time steps")
     args = ap.parse_args()
@@ -217,6 +219,8 @@ def main():
         return run_reference(args)
     if args.profile_batch:
         return profile_batch(args)
+    if args.profile_adjoint:
+        return profile_adjoint(args)
 
     import numpy as np
     import torch
@@ -371,6 +375,27 @@ def profile_batch(args):
     b.step(args.steps)
     torch.cuda.synchronize()
     print(json.dumps({"profile": "batched", "instances": len(inst), "time_steps": args.steps}))
+    return 0
+
+
+def profile_adjoint(args):
+    import numpy as np
+    import torch
+
+    import paper_2312_07010_gb300 as P
+    from workloads import cfg5, tanh_disc
+    w = cfg5()
+    phi0 = torch.from_numpy(w.phi0().astype(np.float32)).cuda()
+    target = torch.from_numpy(tanh_disc(w.n[0], w.h, w.eps).astype(np.float32)).cuda()
+    s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    s.set_state(phi0)
+    s.record_for_grad(w.steps, 50)
+    for _ in range(args.steps):
+        s.set_state(phi0)
+        s.step(w.steps)
+        s.grad(2 * (s.phi - target) / s.numel)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "adjoint", "time_steps": w.steps, "passes": args.steps}))
     return 0
 
 

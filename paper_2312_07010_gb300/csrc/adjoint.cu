@@ -318,14 +318,14 @@ __device__ __forceinline__ void adjoint_block(const T* P, const T* M, const T* _
     }
 }
 
-template <typename T, int BC>
+template <typename T, int BC, int SS>
 __global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ CUtensorMap map_p,
                                                        const __grid_constant__ CUtensorMap map_q,
                                                        const __grid_constant__ CUtensorMap map_l,
                                                        const T* __restrict__ phin, const T* __restrict__ phin1,
                                                        const T* __restrict__ adj1, T* __restrict__ adj0, Geo g,
                                                        Coef<T> cf, int ybchunk, int* err, CSum* part) {
-    using TT = Tile3<T, 2, 2>;
+    using TT = Tile3<T, 2, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, S = TT::S;
     constexpr int BOX = TT::SLOT_STRIDE / sizeof(T);  // elements per box (128-byte aligned)
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -424,9 +424,13 @@ static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin
             if (encode_tensor_map(&mp, sizeof(T), 2, phin, dims2, box) &&
                 encode_tensor_map(&mq, sizeof(T), 2, phin1, dims2, box) &&
                 encode_tensor_map(&ml, sizeof(T), 2, adj1, dims2, box)) {
-                const size_t smem = 128 + TT::BAR_BYTES + (size_t)TT::S * 3 * TT::SLOT_STRIDE;
-                auto kern =
-                    bc == 0 ? k_adjoint2d_tma<T, 0> : (bc == 1 ? k_adjoint2d_tma<T, 1> : k_adjoint2d_tma<T, 2>);
+                // one block per CTA needs one ring slot: more CTAs fit on an SM
+                const int S = ybchunk == 1 ? 1 : 2;
+                const size_t smem = 128 + TT::BAR_BYTES + (size_t)S * 3 * TT::SLOT_STRIDE;
+                auto kern = S == 1 ? (bc == 0 ? k_adjoint2d_tma<T, 0, 1>
+                                              : (bc == 1 ? k_adjoint2d_tma<T, 1, 1> : k_adjoint2d_tma<T, 2, 1>))
+                                   : (bc == 0 ? k_adjoint2d_tma<T, 0, 2>
+                                              : (bc == 1 ? k_adjoint2d_tma<T, 1, 2> : k_adjoint2d_tma<T, 2, 2>));
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
                 kern<<<dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), smem, st>>>(
