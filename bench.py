@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--depth", type=int, default=1)
     ap.add_argument("--profile", action="store_true",
                     help="only set up the 512^3 workload and run --steps time steps (for ncu captures)")
+    ap.add_argument("--profile-lines", action="store_true",
+                    help="only set up the 4096-line 1D workload and run --steps time steps")
     ap.add_argument("--profile-adjoint", action="store_true",
                     help="only run --steps forward+backward passes of the 1024^2 adjoint workload")
     ap.add_argument("--profile-batch", action="store_true",
@@ -221,6 +223,8 @@ def main():
         return profile_batch(args)
     if args.profile_adjoint:
         return profile_adjoint(args)
+    if args.profile_lines:
+        return profile_lines(args)
 
     import numpy as np
     import torch
@@ -378,6 +382,22 @@ def profile_batch(args):
     return 0
 
 
+def profile_lines(args):
+    import numpy as np
+    import torch
+
+    import paper_2312_07010_gb300 as P
+    from workloads import line_instances
+    lines = line_instances()
+    L = P.Lines([i.n for i in lines], [i.eps for i in lines], [i.dt for i in lines], [i.h for i in lines],
+                [i.bc for i in lines], "f32")
+    L.set_states([i.phi0().astype(np.float32) for i in lines])
+    L.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "lines", "lines": len(lines), "time_steps": args.steps}))
+    return 0
+
+
 def profile_adjoint(args):
     import numpy as np
     import torch
@@ -505,6 +525,35 @@ def extras(P, args):
                                   "fwd_bwd_over_plain_fwd": ms_fb / ms_p}
     s.close()
     del s
+    torch.cuda.empty_cache()
+    # batched lines: 4096 1D problems (lengths log-uniform in [32, 4096], seed 4), FP32,
+    # 2000 steps in one call, against single-line runs of a 64-line sample
+    from workloads import LINE_STEPS, line_instances
+    lines = line_instances()
+    Lb = P.Lines([i.n for i in lines], [i.eps for i in lines], [i.dt for i in lines], [i.h for i in lines],
+                 [i.bc for i in lines], "f32")
+    lstates = [i.phi0().astype(np.float32) for i in lines]
+    Lb.set_states(lstates)
+    ms_l = _time(lambda: Lb.step(LINE_STEPS), 2)
+    lunits = sum(i.n for i in lines) * LINE_STEPS
+    sample = lines[:: len(lines) // 64][:64]
+    singles = []
+    for i in sample:
+        s1 = P.AllenCahn((i.n,), i.eps, i.dt, i.h, i.bc, "f32")
+        s1.set_state(i.phi0().astype(np.float32))
+        singles.append(s1)
+
+    def seq_lines():
+        for s1 in singles:
+            s1.step(LINE_STEPS)
+    ms_s = _time(seq_lines, 1)
+    sunits = sum(i.n for i in sample) * LINE_STEPS
+    out["lines_4096_1d"] = {"glups": lunits / (ms_l * 1e-3) / 1e9, "ms": ms_l, "lines": len(lines),
+                            "unknowns": sum(i.n for i in lines), "steps": LINE_STEPS,
+                            "sequential_single_glups": sunits / (ms_s * 1e-3) / 1e9,
+                            "sequential_sample": "64 lines, same lengths distribution"}
+    del singles
+    Lb.close()
     torch.cuda.empty_cache()
     # the collide-and-stream population form on the 512^3 workload, against the FD form:
     # per update it writes and reads 2d+1 populations (collide: 1 read + 7 writes; stream:

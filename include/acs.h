@@ -52,6 +52,7 @@ extern "C" {
 
 typedef struct acs_ctx acs_ctx;
 typedef struct acs_batch acs_batch;
+typedef struct acs_lines acs_lines;
 
 /* Boundary conditions (Sec. I: HN-BC, HD-BC, P-BC; matrices of Eq. Ddeltax). */
 enum { ACS_BC_PERIODIC = 0, ACS_BC_NEUMANN = 1, ACS_BC_DIRICHLET = 2 };
@@ -346,6 +347,40 @@ ACS_API int acs_batch_observe(acs_batch* b, double* h_energy, double* h_maxnorm)
  * GPU fault is involved. */
 ACS_API int acs_batch_inject_fault(acs_batch* b, int mode);
 ACS_API void acs_batch_destroy(acs_batch* b);
+
+/*
+ * Batched lines: `count` independent 1D problems (Eq. IE-FD with d = 1) of n[i]
+ * unknowns, each with its own eps, dt, h and boundary (Eq. Ddeltax at both ends).  The
+ * paper's 1D runs (Table 2, Fig. 4) are such lines; this is many of them at once.  A
+ * line of up to 1024 unknowns (FP64: 512) is held in one warp's registers and a longer
+ * one (up to 28672, FP64 14336) in one CTA's shared memory for all the steps of a call,
+ * so the state touches device memory only at the call's start and end; lines of
+ * different size classes run concurrently.  Each line's state is bit-identical to
+ * acs_step() on that line alone.
+ *
+ * Layout: line i is the n[i] values at element offsets[i] (acs_lines_offsets) of one
+ * device buffer of acs_lines_numel() elements; lines start on 16-byte boundaries.
+ *
+ * acs_lines_create  validates every line as acs_create does (dims = 1) and rejects
+ *                   lines longer than the limits above (ACS_E_INVAL; acs_step handles
+ *                   those); returns the strongest ACS_WARN_* over the lines.  The
+ *                   caller owns *out (acs_lines_destroy).
+ * acs_lines_bind    d_phi: the packed states (16-byte aligned); d_work:
+ *                   acs_lines_work_bytes() bytes, 256-byte aligned; both caller-owned and
+ *                   valid while bound; stream: where every call is enqueued.
+ * acs_lines_step    advances every line n_steps (asynchronous on the stream).
+ * acs_lines_observe per-line E_h and max|phi| into host arrays of `count` doubles
+ *                   (synchronizes).
+ */
+ACS_API int acs_lines_create(int count, const int64_t* n, const double* eps, const double* dt,
+                             const double* h, const int* bc, int dtype, acs_lines** out);
+ACS_API size_t acs_lines_numel(const acs_lines* L);
+ACS_API int acs_lines_offsets(const acs_lines* L, int64_t* offsets);
+ACS_API size_t acs_lines_work_bytes(const acs_lines* L);
+ACS_API int acs_lines_bind(acs_lines* L, void* d_phi, void* d_work, size_t work_bytes, void* stream);
+ACS_API int acs_lines_step(acs_lines* L, int64_t n_steps);
+ACS_API int acs_lines_observe(acs_lines* L, double* h_energy, double* h_maxnorm);
+ACS_API void acs_lines_destroy(acs_lines* L);
 
 #ifdef __cplusplus
 }

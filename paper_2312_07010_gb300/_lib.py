@@ -71,6 +71,15 @@ SIGNATURES = {
     "acs_batch_observe": (_c.c_int, [_vp, _dp, _dp]),
     "acs_batch_inject_fault": (_c.c_int, [_vp, _c.c_int]),
     "acs_batch_destroy": (None, [_vp]),
+    "acs_lines_create": (_c.c_int, [_c.c_int, _i64p, _dp, _dp, _dp, _c.POINTER(_c.c_int), _c.c_int,
+                                    _c.POINTER(_vp)]),
+    "acs_lines_numel": (_c.c_size_t, [_vp]),
+    "acs_lines_offsets": (_c.c_int, [_vp, _i64p]),
+    "acs_lines_work_bytes": (_c.c_size_t, [_vp]),
+    "acs_lines_bind": (_c.c_int, [_vp, _vp, _vp, _c.c_size_t, _vp]),
+    "acs_lines_step": (_c.c_int, [_vp, _i64]),
+    "acs_lines_observe": (_c.c_int, [_vp, _dp, _dp]),
+    "acs_lines_destroy": (None, [_vp]),
 }
 
 _lib = None

@@ -34,8 +34,9 @@ static void pick_newton(double t, double rb, double tol, int* newton, double* ym
     int n = 3;
     for (int k = 1; k <= 3; ++k)
         if (cubic_bound(yneed, k) <= tol) { n = k; break; }
-    // largest y (up to 0.1) where the bound holds with n corrections
-    double lo = 0.0, hi = 0.1;
+    // largest y (below the series' radius 4/27) where the bound holds with n
+    // corrections; it is at least yneed whenever the bound holds there
+    double lo = 0.0, hi = 0.999 * 4.0 / 27.0;
     if (cubic_bound(hi, n) <= tol) lo = hi;
     else
         for (int it = 0; it < 80; ++it) {
@@ -129,7 +130,7 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
         pick_newton(t, rb, tol, &c.newton, &ymax);
         c.ymax = (T)ymax;
         c.seed = 0;
-        if (c.solve == kSolveNewton && cubic_bound(yneed, c.newton) > tol) {
+        if (c.solve == kSolveNewton && (cubic_bound(yneed, c.newton) > tol || ymax < yneed)) {
             // the three-term seed does not cover |xi| <= 1.001: the rational seed does
             const int k = pick_rational(a, b, tol, NewtonMax<T>::value);
             c.seed = 1;

@@ -144,3 +144,27 @@ def test_lb_form_host_logic(L):
             assert L.acs_set_scheme(ctx, 1) == -7
             assert L.acs_set_scheme(ctx, 0) == 0
             L.acs_destroy(ctx)
+
+
+def test_lines_create_limits(L):
+    """Batched lines: per-line validation and the on-chip length limits (host only)."""
+    def create(ns, dtype=0):
+        k = len(ns)
+        h = ctypes.c_void_p()
+        rc = L.acs_lines_create(k, (ctypes.c_int64 * k)(*ns), (ctypes.c_double * k)(*([0.02] * k)),
+                                (ctypes.c_double * k)(*([0.01] * k)), (ctypes.c_double * k)(*([0.1] * k)),
+                                (ctypes.c_int * k)(*([1] * k)), dtype, ctypes.byref(h))
+        return rc, h
+    rc, h = create([1, 5, 33, 2048, 28672])
+    assert rc == 0
+    offs = (ctypes.c_int64 * 5)()
+    assert L.acs_lines_offsets(h, offs) == 0
+    assert list(offs) == [0, 4, 12, 48, 2096]
+    assert L.acs_lines_numel(h) == 2096 + 28672
+    L.acs_lines_destroy(h)
+    assert create([28673])[0] == -1
+    rc, h = create([14336], 1)
+    assert rc == 0
+    L.acs_lines_destroy(h)
+    assert create([14337], 1)[0] == -1
+    assert create([0])[0] == -1

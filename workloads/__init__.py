@@ -198,3 +198,39 @@ def batched_instances(count: int = 256, seed: int = 2, n_lo: int = 64, n_hi: int
 
 
 BATCH_STEPS = 500
+
+
+@dataclass
+class LineInstance:
+    n: int
+    h: float
+    eps: float
+    dt: float
+    bc: int
+    seed: int
+
+    def phi0(self) -> np.ndarray:
+        return uniform_field((self.n,), -1.0, 1.0, self.seed)
+
+
+def line_instances(count: int = 4096, seed: int = 4, n_lo: int = 32, n_hi: int = 4096) -> List[LineInstance]:
+    """Lines of the batched 1D workload: length log-uniform in [n_lo, n_hi], eps ~
+    U[0.005, 0.03], boundary uniform over {periodic, Neumann, Dirichlet} on the unit
+    interval (h = 1/n, or 1/(n+1) for Dirichlet interior nodes); phi0 ~ U[-1, 1] from
+    the line's own seed (seed*100003 + index); dt by dt_rule for d = 1."""
+    rng = np.random.default_rng(seed)
+    sides = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))
+    sides = np.clip(np.rint(sides).astype(np.int64), n_lo, n_hi)
+    epss = rng.uniform(0.005, 0.03, size=count)
+    bcs = rng.integers(0, 3, size=count)
+    out = []
+    for i in range(count):
+        n = int(sides[i])
+        bc = int(bcs[i])
+        h = 1.0 / (n + 1) if bc == BC_DIRICHLET else 1.0 / n
+        eps = float(epss[i])
+        out.append(LineInstance(n, h, eps, dt_rule(1, eps, h), bc, seed * 100003 + i))
+    return out
+
+
+LINE_STEPS = 2000
