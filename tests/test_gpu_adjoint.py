@@ -145,3 +145,36 @@ def test_grad_requires_recording(acs):
     with pytest.raises(acs.AcsError) as e:
         s.step(1)
     assert e.value.status == -3
+
+
+def test_adjoint_full_size_fp64_dot_product(acs):
+    """The 1024^2 periodic adjoint workload (500 steps, checkpoints every 50) in FP64:
+    the gradient against central differences of the loss along a random direction of
+    phi0 and along eps^2."""
+    w = cfg5()
+    n = w.n[0]
+    phi0 = w.phi0()
+    target = tanh_disc(n, w.h, w.eps)
+    s = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f64")
+    s.set_state(phi0)
+    s.record_for_grad(w.steps, 50)
+    s.step(w.steps)
+    pT = s.numpy()
+    g0, ge = s.grad(torch.from_numpy(2 * (pT - target) / pT.size).cuda())
+    g0 = g0.cpu().numpy()
+
+    def L(ph, eps2):
+        t = acs.AllenCahn(w.n, math.sqrt(eps2), w.dt, w.h, w.bc, "f64")
+        t.set_state(ph)
+        t.step(w.steps)
+        v = float(np.mean((t.numpy() - target) ** 2))
+        t.close()
+        return v
+
+    v = uniform_field((n, n), -1, 1, 91)
+    st = 1e-6
+    fd = (L(phi0 + st * v, w.eps ** 2) - L(phi0 - st * v, w.eps ** 2)) / (2 * st)
+    assert float(np.sum(g0 * v)) == pytest.approx(fd, rel=1e-6)
+    se = 1e-7
+    fde = (L(phi0, w.eps ** 2 + se) - L(phi0, w.eps ** 2 - se)) / (2 * se)
+    assert ge == pytest.approx(fde, rel=1e-5)

@@ -127,3 +127,26 @@ def test_batch_barrier_timeout_is_reported(acs):
     b.step(4)
     E, M = b.observe()
     assert np.isfinite(E).all() and (M <= 1.0).all()
+
+
+def test_batch_full_workload(acs):
+    """The benchmark's 256-instance workload (sides 64..1024, 500 steps in one call):
+    every instance equals its standalone run bit for bit, keeps |phi| <= 1, and its
+    E_h does not increase."""
+    from workloads import BATCH_STEPS
+    inst = batched_instances()
+    b = acs.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+                  [i.bc for i in inst], "f32")
+    phi0 = [i.phi0().astype(np.float32) for i in inst]
+    b.set_states(phi0)
+    E0, _ = b.observe()
+    b.step(BATCH_STEPS)
+    E1, M1 = b.observe()
+    got = b.states()
+    assert np.all(E1 <= E0) and np.all(M1 <= 1.0)
+    for k, i in enumerate(inst):
+        s = acs.AllenCahn((i.n, i.n), i.eps, i.dt, i.h, i.bc, "f32")
+        s.set_state(phi0[k])
+        s.step(BATCH_STEPS)
+        assert np.array_equal(got[k], s.numpy()), k
+        s.close()

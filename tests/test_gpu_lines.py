@@ -97,3 +97,27 @@ def test_lines_stationary_profile(acs):
     # second-order spatial error: halving h divides the drift by about four
     assert errs[0] > errs[1] > errs[2]
     assert errs[0] / errs[2] > 10
+
+
+def test_lines_full_workload(acs):
+    """The benchmark's 4096-line workload (lengths 32..4096, 2000 steps in one call):
+    a sample of 128 lines equals its standalone runs bit for bit; every line keeps
+    |phi| <= 1 and a non-increasing E_h."""
+    from workloads import LINE_STEPS, line_instances
+    lines = line_instances()
+    L = acs.Lines([i.n for i in lines], [i.eps for i in lines], [i.dt for i in lines], [i.h for i in lines],
+                  [i.bc for i in lines], "f32")
+    phi0 = [i.phi0().astype(np.float32) for i in lines]
+    L.set_states(phi0)
+    E0, _ = L.observe()
+    L.step(LINE_STEPS)
+    E1, M1 = L.observe()
+    assert np.all(E1 <= E0) and np.all(M1 <= 1.0)
+    got = L.states()
+    for k in range(0, len(lines), len(lines) // 128):
+        i = lines[k]
+        s = acs.AllenCahn((i.n,), i.eps, i.dt, i.h, i.bc, "f32")
+        s.set_state(phi0[k])
+        s.step(LINE_STEPS)
+        assert np.array_equal(got[k], s.numpy()), k
+        s.close()
