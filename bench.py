@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--depth", type=int, default=1)
     ap.add_argument("--profile", action="store_true",
                     help="only set up the 512^3 workload and run --steps time steps (for ncu captures)")
+    ap.add_argument("--profile-lb", action="store_true",
+                    help="only run --steps time steps of the collide-and-stream form on 256^3 Neumann FP32")
     ap.add_argument("--profile-lines", action="store_true",
                     help="only set up the 4096-line 1D workload and run --steps time steps")
     ap.add_argument("--profile-adjoint", action="store_true",
@@ -225,6 +227,8 @@ def main():
         return profile_adjoint(args)
     if args.profile_lines:
         return profile_lines(args)
+    if args.profile_lb:
+        return profile_lb(args)
 
     import numpy as np
     import torch
@@ -379,6 +383,23 @@ def profile_batch(args):
     b.step(args.steps)
     torch.cuda.synchronize()
     print(json.dumps({"profile": "batched", "instances": len(inst), "time_steps": args.steps}))
+    return 0
+
+
+def profile_lb(args):
+    import numpy as np
+    import torch
+
+    import paper_2312_07010_gb300 as P
+    from workloads import dt_rule, uniform_field
+    n, eps = 256, 0.01
+    h = 1.0 / n
+    s = P.AllenCahn((n, n, n), eps, dt_rule(3, eps, h), h, P.ACS_BC_NEUMANN, "f32")
+    s.use_lb_form()
+    s.set_state(uniform_field((n, n, n), -1, 1, 1).astype(np.float32))
+    s.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "lb_form", "n": n, "time_steps": args.steps}))
     return 0
 
 

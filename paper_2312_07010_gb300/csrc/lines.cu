@@ -94,13 +94,20 @@ __global__ void __launch_bounds__(64) k_lines_warp(T* phi, const LineRec<T>* __r
     ACS_SOLVE_DISPATCH(L.c.solve, SV, line_warp<T, R, SV>(phi, L, nsteps));
 }
 
-// One CTA per line in shared memory: buffers of n + 2 values (ghosts at both ends).
+// One CTA per line in shared memory: buffers of n + 2 values (ghosts at both ends),
+// padded to a multiple of 4 with zeros.  Each thread updates groups of 4 consecutive
+// points with the multi-point root solve (the per-point values, see roots()).
 template <typename T, int SOLVE>
 __device__ __forceinline__ void line_cta(T* __restrict__ phi, const LineRec<T>& L, int64_t nsteps, T* A, T* B) {
+    constexpr int G = 4;
     const int n = L.n, bc = L.bc;
+    const int npad = (n + G - 1) / G * G;
     const Coef<T> c = L.c;
     T* p = phi + L.off;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) A[i + 1] = p[i];
+    for (int i = threadIdx.x; i < npad + 2; i += blockDim.x) {
+        A[i] = i >= 1 && i <= n ? p[i - 1] : T(0);
+        B[i] = T(0);
+    }
     for (int64_t s = 0; s < nsteps; ++s) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -108,8 +115,18 @@ __device__ __forceinline__ void line_cta(T* __restrict__ phi, const LineRec<T>& 
             A[n + 1] = bc == ACS_BC_PERIODIC ? A[1] : (bc == ACS_BC_NEUMANN ? A[n] : T(0));
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            B[i + 1] = update<T, SOLVE>(A[i + 1], nsum(A[i], A[i + 2]), c);
+        for (int g0 = threadIdx.x * G; g0 < n; g0 += blockDim.x * G) {
+            T v[G + 2], xi[G], out[G];
+#pragma unroll
+            for (int k = 0; k < G + 2; ++k) v[k] = A[g0 + k];  // points g0 - 1 .. g0 + G
+            // points past n read the ghost and the zero padding; their results are unused
+#pragma unroll
+            for (int k = 0; k < G; ++k) xi[k] = predictor(v[k + 1], nsum(v[k], v[k + 2]), c);
+            roots<T, SOLVE, G>(xi, out, c);
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (g0 + k < n) B[g0 + k + 1] = out[k];
+        }
         T* t = A;
         A = B;
         B = t;
@@ -123,7 +140,7 @@ __global__ void __launch_bounds__(256) k_lines_cta(T* phi, const LineRec<T>* __r
                                                    const int* __restrict__ ids, int64_t nsteps, int maxn) {
     extern __shared__ __align__(16) unsigned char sm[];
     T* A = reinterpret_cast<T*>(sm);
-    T* B = A + (maxn + 2);
+    T* B = A + ((maxn + 3) / 4 * 4 + 2);
     const LineRec<T>& L = lines[ids[blockIdx.x]];
     ACS_SOLVE_DISPATCH(L.c.solve, SV, line_cta<T, SV>(phi, L, nsteps, A, B));
 }
@@ -216,7 +233,7 @@ cudaError_t launch_class(acs_lines* L, int k, int64_t nsteps, cudaStream_t st) {
                 break;
         }
     } else {
-        const size_t smem = 2 * (size_t)(L->maxn_cta + 2) * sizeof(T);
+        const size_t smem = 2 * (size_t)((L->maxn_cta + 3) / 4 * 4 + 2) * sizeof(T);
         cudaError_t e = cudaFuncSetAttribute(k_lines_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_lines_cta<T><<<cnt, 256, smem, st>>>(phi, rec, ids, nsteps, L->maxn_cta);
