@@ -47,11 +47,11 @@ struct BlockRef {
     int inst, x0, y0, colx, rowy, pad0, pad1, pad2;
 };
 
-// Tile geometry of the batched kernel: 2 rows per thread, 6 ring slots; blocks are
+// Tile geometry of the batched kernel: 2 rows per thread, 4 ring slots; blocks are
 // handed out in chunks of kChunk consecutive blocks (one tensor-map set per instance:
 // main box, column box, row box, for each of the two state buffers).
 template <typename T>
-using BatchTile = Tile3<T, 2, 6>;
+using BatchTile = Tile3<T, 2, 4>;
 constexpr int kChunk = 4;
 constexpr int kMapsPerInst = 6;
 constexpr int kFenceWords = 64;  // instances whose maps a CTA remembers as acquired
@@ -236,7 +236,7 @@ __device__ __forceinline__ void batch_block_any(const T* cur, const T* colb, con
 // warp) that every warp is done with it, so no compute warp waits for another and
 // only the producer waits, before it refills a slot.
 template <typename T>
-__global__ void __launch_bounds__(288, 3) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
+__global__ void __launch_bounds__(288, sizeof(T) == 4 ? 4 : 3) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
                                                  const CUtensorMap* __restrict__ maps, int count,
                                                  const BlockRef* __restrict__ blocks, int nblocks, int nsteps,
                                                  BarrierState* bs, int* err) {
