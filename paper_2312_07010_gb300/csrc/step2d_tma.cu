@@ -1,13 +1,13 @@
 // step2d_tma.cu -- one RLB-MIE-FD step (Eq. IE-FD, Remark 1) on a 2D grid whose rows
-// are a multiple of 16 bytes, streaming TMA-staged blocks of 16 rows.
+// are a multiple of 16 bytes, streaming TMA-staged blocks of 8 RPT rows.
 //
-// A CTA owns a column of TX unknowns (128 FP32 / 64 FP64) and a run of 16-row
-// blocks.  One thread issues a TMA load of each block plus a one-cell halo (rows
-// y0 - 1 .. y0 + 16, the x halo widened to a 16-byte group) into a 4-slot ring, up
-// to four blocks ahead; each of the 256 threads owns one 16-byte vector in two rows
-// and takes its x neighbours from its registers and warp shuffles, its y neighbours
-// from shared memory.  Boundaries as in the 3D kernel: TMA zero fill for Dirichlet,
-// per-row fix-ups (own value / wrapped global read) for Neumann and periodic.
+// A CTA owns a column of TX unknowns (128 FP32 / 64 FP64) and a run of row blocks.
+// One thread issues a TMA load of each block plus a one-cell halo (the x halo widened
+// to a 16-byte group) into a ring of S slots (RPT and S are the tile variant), S blocks
+// ahead; each of the 256 threads owns one 16-byte vector in RPT rows and takes its x
+// neighbours from its registers and warp shuffles, its y neighbours from shared
+// memory.  Boundaries as in the 3D kernel: TMA zero fill for Dirichlet, per-row
+// fix-ups (own value / wrapped global read) for Neumann and periodic.
 #include <type_traits>
 
 #include "acs_host.h"
@@ -17,9 +17,9 @@
 namespace acs {
 
 template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_step2d_tma(const __grid_constant__ CUtensorMap tmap,
-                                                    const T* __restrict__ src, T* __restrict__ dst, Geo g,
-                                                    Coef<T> c, int ybchunk, int* err, RedPartial* part) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2)
+    k_step2d_tma(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src, T* __restrict__ dst, Geo g,
+                 Coef<T> c, int ybchunk, int* err, RedPartial* part) {
     using TT = Tile3<T, RPT, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);

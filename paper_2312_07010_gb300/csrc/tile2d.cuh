@@ -2,7 +2,7 @@
 // one-cell halo is staged with cp.async (ghost rules of Eq. Ddeltax applied while
 // loading, so the compute is the same for every point), then each thread updates
 // its points.  Used by the single-problem 2D kernel for rows that are not a multiple
-// of 16 bytes, by the 2D adjoint, and by the batched persistent kernel.
+// of 16 bytes and by the 2D adjoint for such rows.
 //
 // Layout of a staged tile: TY + 2 rows of BW values; the tile's interior starts at
 // column VX (one 16-byte vector) so each thread can read its VX values as one
