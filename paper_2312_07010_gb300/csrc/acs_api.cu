@@ -302,20 +302,9 @@ static cudaError_t enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st) {
 
 static int maybe_autotune(acs_ctx* c);
 
-static int run_steps(acs_ctx* c, int64_t n) {
-    if (n <= 0) return ACS_OK;
-    if (int rc = maybe_autotune(c)) return rc;
-    if (c->grad.active) {
-        int rc = grad_record_steps(c, n);
-        if (rc) return rc;
-        c->steps_done += n;
-        return ACS_OK;
-    }
-    if (n < 4) {
-        if (enqueue_steps(c, n, c->stream) != cudaSuccess) return ACS_E_CUDA;
-        c->steps_done += n;
-        return ACS_OK;
-    }
+// Replay (recording on first use) the graph of exactly n steps.
+static int launch_graph(acs_ctx* c, int64_t n) {
+    if (n < 4) return enqueue_steps(c, n, c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
     GraphEntry* hit = nullptr;
     for (auto& e : c->graphs)
         if (e.nsteps == n && e.kernel == c->kernel && e.depth == c->depth && e.scheme == c->scheme) hit = &e;
@@ -340,7 +329,27 @@ static int run_steps(acs_ctx* c, int64_t n) {
         c->graphs.push_back(GraphEntry{n, c->kernel, c->depth, c->scheme, exec});
         hit = &c->graphs.back();
     }
-    if (cudaGraphLaunch(hit->exec, c->stream) != cudaSuccess) return ACS_E_CUDA;
+    return cudaGraphLaunch(hit->exec, c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+}
+
+// Long runs replay a graph of kGraphSteps steps (each ends with the state back in
+// phi) as often as needed plus one of the remainder, so graphs stay small.
+constexpr int64_t kGraphSteps = 1024;
+
+static int run_steps(acs_ctx* c, int64_t n) {
+    if (n <= 0) return ACS_OK;
+    if (int rc = maybe_autotune(c)) return rc;
+    if (c->grad.active) {
+        int rc = grad_record_steps(c, n);
+        if (rc) return rc;
+        c->steps_done += n;
+        return ACS_OK;
+    }
+    for (int64_t left = n; left > 0;) {
+        const int64_t k = left > kGraphSteps ? kGraphSteps : left;
+        if (int rc = launch_graph(c, k)) return rc;
+        left -= k;
+    }
     c->steps_done += n;
     return ACS_OK;
 }

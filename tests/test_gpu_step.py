@@ -124,6 +124,23 @@ def test_step_calls_compose(acs):
     assert a.steps_done == 37
 
 
+def test_long_runs_replay_bounded_graphs(acs):
+    """A run longer than one recorded graph (1024 steps) replays it and a remainder:
+    2500 steps in one call equal 1250 + 1250, bit for bit, and match the oracle (FP64)."""
+    shape = (24, 20)
+    h, eps, dt, phi0 = _problem(shape, BC_PERIODIC, 8)
+    a = acs.AllenCahn(shape, eps, dt, h, BC_PERIODIC, "f64")
+    b = acs.AllenCahn(shape, eps, dt, h, BC_PERIODIC, "f64")
+    a.set_state(phi0)
+    b.set_state(phi0)
+    a.step(2500)
+    b.step(1250)
+    b.step(1250)
+    assert np.array_equal(a.numpy(), b.numpy())
+    assert a.steps_done == 2500
+    assert relerr(a.numpy(), oracle.run_fd(phi0, eps, dt, h, BC_PERIODIC, 2500)) <= 1e-12
+
+
 @pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
 def test_fex_scheme_parity(acs, bc):
     shape = (21, 34)
