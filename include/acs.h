@@ -53,6 +53,7 @@ extern "C" {
 typedef struct acs_ctx acs_ctx;
 typedef struct acs_batch acs_batch;
 typedef struct acs_lines acs_lines;
+typedef struct acs_pipe acs_pipe;
 
 /* Boundary conditions (Sec. I: HN-BC, HD-BC, P-BC; matrices of Eq. Ddeltax). */
 enum { ACS_BC_PERIODIC = 0, ACS_BC_NEUMANN = 1, ACS_BC_DIRICHLET = 2 };
@@ -381,6 +382,48 @@ ACS_API int acs_lines_bind(acs_lines* L, void* d_phi, void* d_work, size_t work_
 ACS_API int acs_lines_step(acs_lines* L, int64_t n_steps);
 ACS_API int acs_lines_observe(acs_lines* L, double* h_energy, double* h_maxnorm);
 ACS_API void acs_lines_destroy(acs_lines* L);
+
+/*
+ * Pipelined host-to-host runs: a stream of independent jobs, each "copy phi^0 from
+ * host memory, advance n_steps steps of Eq. IE-FD (logging E_h and max|phi| every
+ * `every` steps, as acs_run_logged), copy phi^N back to host memory".  `slots` device
+ * states (2 to 4) take consecutive jobs in turn, so the host-to-device copy of a later
+ * job and the device-to-host copy of an earlier one run on their own streams while a
+ * job computes on the bound stream.  Every job's results are those of
+ * acs_set_state_host, acs_run_logged and acs_get_state_host on one context, bit for bit.
+ *
+ * acs_pipe_create   validates as acs_create does (and 2 <= slots <= 4, else
+ *                   ACS_E_INVAL) and returns its status; the caller owns *out
+ *                   (acs_pipe_destroy).  Host-only (no CUDA call).
+ * acs_pipe_bytes    device bytes acs_pipe_bind needs: one state and one work area
+ *                   (acs_work_bytes) per slot, each rounded up to 256 bytes.
+ * acs_pipe_bind     d_buf: acs_pipe_bytes() bytes of device memory, 256-byte aligned,
+ *                   caller-owned and valid while bound; stream: where the steps run.
+ *                   Creates the two copy streams and the events the library owns.
+ * acs_pipe_context  slot in [0, slots): the context that runs that slot's jobs, for
+ *                   acs_set_kernel / acs_set_scheme / acs_set_variant (apply the same
+ *                   setting to every slot).  Owned by the pipe; never destroy or rebind it.
+ * acs_pipe_submit   enqueues one job and returns without waiting.  h_in (read) and
+ *                   h_out (written): n[0] x ... x n[dims-1] values of the dtype;
+ *                   h_log: 2 (n_steps / every + 1) doubles {E_h, max|phi|} per entry, or
+ *                   null with every = 0 (no logging; ACS_E_INVAL if every < 0, or if
+ *                   h_log is null while every > 0, or more than 4096 entries).  The
+ *                   host buffers must stay valid and untouched until acs_pipe_wait
+ *                   returns; page-locked buffers are what lets the copies overlap
+ *                   (pageable ones work, serialized).
+ * acs_pipe_wait     waits for every submitted job; ACS_E_TIMEOUT if a kernel's bounded
+ *                   wait gave up, ACS_E_NONFINITE if a logged value is NaN/Inf (the
+ *                   outputs are still written), else ACS_OK.
+ */
+ACS_API int acs_pipe_create(int dims, const int64_t n[3], double eps, double dt, double h, int bc, int dtype,
+                            int slots, acs_pipe** out);
+ACS_API size_t acs_pipe_bytes(const acs_pipe* p);
+ACS_API int acs_pipe_bind(acs_pipe* p, void* d_buf, size_t bytes, void* stream);
+ACS_API acs_ctx* acs_pipe_context(acs_pipe* p, int slot);
+ACS_API int acs_pipe_submit(acs_pipe* p, const void* h_in, void* h_out, int64_t n_steps, int64_t every,
+                            double* h_log);
+ACS_API int acs_pipe_wait(acs_pipe* p);
+ACS_API void acs_pipe_destroy(acs_pipe* p);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ __all__ = [
     "ACS_BC_PERIODIC", "ACS_BC_NEUMANN", "ACS_BC_DIRICHLET", "ACS_F32", "ACS_F64",
     "ACS_KERNEL_AUTO", "ACS_KERNEL_NAIVE", "ACS_KERNEL_TILED", "ACS_KERNEL_TEMPORAL",
     "ACS_SCHEME_RLB_MIE_FD", "ACS_SCHEME_FEX_FD",
-    "AllenCahn", "AllenCahnFunction", "allen_cahn", "Batch", "Lines", "dt_max",
+    "AllenCahn", "AllenCahnFunction", "allen_cahn", "Batch", "Lines", "Pipeline", "dt_max",
 ]
 
 
@@ -31,4 +31,7 @@ def __getattr__(name):
     if name == "Lines":
         from . import lines
         return lines.Lines
+    if name == "Pipeline":
+        from . import pipeline
+        return pipeline.Pipeline
     raise AttributeError(name)

@@ -80,6 +80,14 @@ SIGNATURES = {
     "acs_lines_step": (_c.c_int, [_vp, _i64]),
     "acs_lines_observe": (_c.c_int, [_vp, _dp, _dp]),
     "acs_lines_destroy": (None, [_vp]),
+    "acs_pipe_create": (_c.c_int, [_c.c_int, _i64p, _c.c_double, _c.c_double, _c.c_double, _c.c_int, _c.c_int,
+                                   _c.c_int, _c.POINTER(_vp)]),
+    "acs_pipe_bytes": (_c.c_size_t, [_vp]),
+    "acs_pipe_bind": (_c.c_int, [_vp, _vp, _c.c_size_t, _vp]),
+    "acs_pipe_context": (_vp, [_vp, _c.c_int]),
+    "acs_pipe_submit": (_c.c_int, [_vp, _vp, _vp, _i64, _i64, _dp]),
+    "acs_pipe_wait": (_c.c_int, [_vp]),
+    "acs_pipe_destroy": (None, [_vp]),
 }
 
 _lib = None

@@ -400,6 +400,25 @@ cudaError_t ctx_launch_one(acs_ctx* c, const void* src, void* dst, cudaStream_t 
         return launch_step_naive<float>(c->dims, c->bc, (const float*)src, (float*)dst, c->g, c->cf, st);
     return launch_step_naive<double>(c->dims, c->bc, (const double*)src, (double*)dst, c->g, c->cd, st);
 }
+// Enqueue n_steps steps with {E_h, max|phi|} of the states 0, every, 2 every, ...
+// written to the context's device log (2 doubles per entry); nothing synchronizes.
+int ctx_enqueue_logged(acs_ctx* c, int64_t n_steps, int64_t every, double** d_log, int64_t* entries) {
+    if (!c->bound) return ACS_E_STATE;
+    const int64_t m = every > 0 ? n_steps / every + 1 : 0;
+    if (m > kLogCap) return ACS_E_INVAL;
+    *d_log = c->log;
+    *entries = m;
+    if (m == 0) return run_steps(c, n_steps);
+    if (enqueue_reduce(c, c->phi, c->log, c->stream) != cudaSuccess) return ACS_E_CUDA;
+    int64_t done = 0;
+    for (int64_t k = 1; k < m; ++k) {
+        if (int rc = run_steps(c, every)) return rc;
+        done += every;
+        if (enqueue_reduce(c, c->phi, c->log + 2 * k, c->stream) != cudaSuccess) return ACS_E_CUDA;
+    }
+    return run_steps(c, n_steps - done);
+}
+int ctx_check_err(acs_ctx* c) { return check_err_flag(c); }
 CtxView ctx_view(acs_ctx* c) {
     CtxView v;
     v.dims = c->dims; v.bc = c->bc; v.dtype = c->dtype; v.g = c->g; v.esize = c->esize;
@@ -679,23 +698,11 @@ ACS_API int acs_phase_volume(acs_ctx* c, double* out_host) {
 
 ACS_API int acs_run_logged(acs_ctx* c, int64_t n_steps, int64_t every, double* h_energy, double* h_maxnorm) {
     if (!c || n_steps < 0 || every < 1 || !h_energy || !h_maxnorm) return ACS_E_INVAL;
-    if (!c->bound) return ACS_E_STATE;
-    const int64_t entries = n_steps / every + 1;
-    if (entries > kLogCap) return ACS_E_INVAL;
-    if (enqueue_reduce(c, c->phi, c->log, c->stream) != cudaSuccess) return ACS_E_CUDA;
-    int64_t done = 0;
-    for (int64_t k = 1; k < entries; ++k) {
-        int rc = run_steps(c, every);
-        if (rc) return rc;
-        done += every;
-        if (enqueue_reduce(c, c->phi, c->log + 2 * k, c->stream) != cudaSuccess) return ACS_E_CUDA;
-    }
-    if (n_steps > done) {
-        int rc = run_steps(c, n_steps - done);
-        if (rc) return rc;
-    }
+    double* d_log = nullptr;
+    int64_t entries = 0;
+    if (int rc = ctx_enqueue_logged(c, n_steps, every, &d_log, &entries)) return rc;
     std::vector<double> buf(2 * entries);
-    if (cudaMemcpyAsync(buf.data(), c->log, sizeof(double) * 2 * entries, cudaMemcpyDeviceToHost, c->stream) !=
+    if (cudaMemcpyAsync(buf.data(), d_log, sizeof(double) * 2 * entries, cudaMemcpyDeviceToHost, c->stream) !=
         cudaSuccess)
         return ACS_E_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ACS_E_CUDA;

@@ -65,6 +65,10 @@ cudaError_t ctx_enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st);
 cudaError_t ctx_launch_one(acs_ctx* c, const void* src, void* dst, cudaStream_t st);
 CtxView ctx_view(acs_ctx* c);
 
+// Implemented in acs_api.cu for the pipelined host-to-host runner (pipe.cu).
+int ctx_enqueue_logged(acs_ctx* c, int64_t n_steps, int64_t every, double** d_log, int64_t* entries);
+int ctx_check_err(acs_ctx* c);  // after a synchronization: ACS_E_TIMEOUT if a kernel gave up
+
 // Tuning cache (tune_cache.cu): a text file of the autotuner's choices.
 bool tune_cache_lookup(int dims, const int64_t* n, int bc, int dtype, int scheme, int* kernel, int* depth,
                        int* variant, int* chunk);

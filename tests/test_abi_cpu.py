@@ -168,3 +168,44 @@ def test_lines_create_limits(L):
     L.acs_lines_destroy(h)
     assert create([14337], 1)[0] == -1
     assert create([0])[0] == -1
+
+
+def test_pipe_host_logic(L):
+    """Pipelined runner: validation as acs_create, two states + two work areas, and the
+    order checks of submit / bind (host only: nothing is bound, nothing is copied)."""
+    def create(dims, n, eps=0.02, dt=0.01, h=0.1, bc=1, dtype=0, slots=2):
+        p = ctypes.c_void_p()
+        nn = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+        return L.acs_pipe_create(dims, nn, eps, dt, h, bc, dtype, slots, ctypes.byref(p)), p
+    for dims, n, dtype, es, slots in ((1, (1000,), 0, 4, 2), (2, (33, 65), 1, 8, 3), (3, (16, 8, 12), 0, 4, 4)):
+        rc, p = create(dims, n, dtype=dtype, slots=slots)
+        assert rc == 0
+        rc2, ctx = _create(L, dims, n, 0.02, 0.01, 0.1, 1, dtype)
+        up = lambda x: (x + 255) // 256 * 256
+        assert L.acs_pipe_bytes(p) == slots * (up(math.prod(n) * es) + up(L.acs_work_bytes(ctx)))
+        L.acs_destroy(ctx)
+        cs = [L.acs_pipe_context(p, k) for k in range(slots)]
+        assert all(cs) and len(set(cs)) == slots
+        assert L.acs_pipe_context(p, slots) is None and L.acs_pipe_context(p, -1) is None
+        one = ctypes.c_void_p(1 << 20)
+        log = (ctypes.c_double * 64)()
+        assert L.acs_pipe_submit(p, one, one, 10, 0, None) == -6      # not bound
+        assert L.acs_pipe_submit(p, one, one, -1, 0, None) == -1
+        assert L.acs_pipe_submit(p, one, one, 10, -1, None) == -1
+        assert L.acs_pipe_submit(p, one, one, 10, 5, None) == -1      # logging needs a log
+        assert L.acs_pipe_submit(p, one, one, 10 ** 6, 1, log) == -1  # more than 4096 entries
+        assert L.acs_pipe_submit(p, None, one, 10, 0, None) == -1
+        assert L.acs_pipe_wait(p) == 0                                # nothing submitted
+        assert L.acs_pipe_bind(p, ctypes.c_void_p((1 << 20) + 16), L.acs_pipe_bytes(p), None) == -1
+        assert L.acs_pipe_bind(p, one, L.acs_pipe_bytes(p) - 1, None) == -3
+        L.acs_pipe_destroy(p)
+    assert create(3, (8, 8, 8), dt=2.5)[0] == -1
+    assert create(4, (8, 8, 8))[0] == -1
+    assert create(3, (8, 8, 8), slots=1)[0] == -1
+    assert create(3, (8, 8, 8), slots=5)[0] == -1
+    rc, p = create(2, (32, 32), eps=0.5, dt=0.5, h=1 / 32)
+    rc2, ctx = _create(L, 2, (32, 32), 0.5, 0.5, 1 / 32, 1)
+    assert rc > 0 and rc == rc2  # the step conditions fail: acs_create's warning
+    L.acs_destroy(ctx)
+    L.acs_pipe_destroy(p)
+    L.acs_pipe_destroy(None)
