@@ -513,6 +513,13 @@ def extras(P, args):
         k, d = s.get_kernel()
         out[name] = {"glups": glups, "ms_per_time_step": ms / nsteps, "hbm_frac_effective": glups * 2 * esz / peak,
                      "kernel": k, "depth": d}
+        if name == "cfg1_fp64_128sq":
+            # the configuration as stated: 1000 steps with E_h and max|phi| every 10
+            def logged():
+                s.run_logged(w.steps, w.log_every)
+            ms = _time(logged, 3)
+            out[name]["logged_every_10_glups"] = w.numel * w.steps / (ms * 1e-3) / 1e9
+            out[name]["logged_every_10_ms"] = ms
         s.close()
         del s, phi0
         torch.cuda.empty_cache()

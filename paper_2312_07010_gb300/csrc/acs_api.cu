@@ -172,7 +172,7 @@ Geo make_geo(int dims, const int64_t* n) {
 using namespace acs;
 
 struct GraphEntry {
-    int64_t nsteps;
+    int64_t nsteps, every;
     int kernel, depth, scheme;
     cudaGraphExec_t exec;
 };
@@ -302,12 +302,32 @@ static cudaError_t enqueue_steps(acs_ctx* c, int64_t n, cudaStream_t st) {
 
 static int maybe_autotune(acs_ctx* c);
 
-// Replay (recording on first use) the graph of exactly n steps.
-static int launch_graph(acs_ctx* c, int64_t n) {
-    if (n < 4) return enqueue_steps(c, n, c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, cudaStream_t st);
+
+// n steps with {E_h, max|phi|} of the states 0, every, 2 every, ... written to the
+// context's log (every = 0: the steps alone).
+static cudaError_t enqueue_run(acs_ctx* c, int64_t n, int64_t every, cudaStream_t st) {
+    if (every <= 0) return enqueue_steps(c, n, st);
+    const int64_t m = n / every + 1;
+    cudaError_t e = enqueue_reduce(c, c->phi, c->log, st);
+    for (int64_t k = 1; k < m && e == cudaSuccess; ++k) {
+        e = enqueue_steps(c, every, st);
+        if (e == cudaSuccess) e = enqueue_reduce(c, c->phi, c->log + 2 * k, st);
+    }
+    const int64_t rest = n - (m - 1) * every;
+    if (e == cudaSuccess && rest > 0) e = enqueue_steps(c, rest, st);
+    return e;
+}
+
+// Replay (recording on first use) the graph of exactly n steps (logged every `every`
+// steps when every > 0), so a whole run costs one launch on the host.
+static int launch_graph(acs_ctx* c, int64_t n, int64_t every = 0) {
+    if (n < 4 && every <= 0) return enqueue_steps(c, n, c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
     GraphEntry* hit = nullptr;
     for (auto& e : c->graphs)
-        if (e.nsteps == n && e.kernel == c->kernel && e.depth == c->depth && e.scheme == c->scheme) hit = &e;
+        if (e.nsteps == n && e.every == every && e.kernel == c->kernel && e.depth == c->depth &&
+            e.scheme == c->scheme)
+            hit = &e;
     if (!hit) {
         if (c->graphs.size() >= 8) {
             cudaGraphExecDestroy(c->graphs.front().exec);
@@ -315,7 +335,7 @@ static int launch_graph(acs_ctx* c, int64_t n) {
         }
         cudaGraph_t graph;
         if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ACS_E_CUDA;
-        cudaError_t e1 = enqueue_steps(c, n, c->cap);
+        cudaError_t e1 = enqueue_run(c, n, every, c->cap);
         cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
             if (e2 == cudaSuccess) cudaGraphDestroy(graph);
@@ -326,7 +346,7 @@ static int launch_graph(acs_ctx* c, int64_t n) {
         cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e3 != cudaSuccess) return ACS_E_CUDA;
-        c->graphs.push_back(GraphEntry{n, c->kernel, c->depth, c->scheme, exec});
+        c->graphs.push_back(GraphEntry{n, every, c->kernel, c->depth, c->scheme, exec});
         hit = &c->graphs.back();
     }
     return cudaGraphLaunch(hit->exec, c->stream) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
@@ -365,7 +385,11 @@ static int check_err_flag(acs_ctx* c) {
 
 static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, cudaStream_t st) {
     const bool rows16 = (c->g.nx * (int64_t)c->esize) % 16 == 0;
-    if ((c->dims == 3 || c->dims == 2) && rows16 && tiled_supported(c->dims, c->dtype, c->g)) {
+    // the reduction follows the step's kernel family: the streamed (tile-per-CTA) pass
+    // with the tiled kernels, the row-per-block one with the one-thread-per-unknown
+    // kernel, which small grids take because it spreads them over more SMs
+    if (c->kernel == ACS_KERNEL_TILED && (c->dims == 3 || c->dims == 2) && rows16 &&
+        tiled_supported(c->dims, c->dtype, c->g)) {
         // the TMA-streamed pipeline: vector loads, neighbours from registers and shuffles
         int np = 0;
         cudaError_t e;
@@ -409,6 +433,13 @@ int ctx_enqueue_logged(acs_ctx* c, int64_t n_steps, int64_t every, double** d_lo
     *d_log = c->log;
     *entries = m;
     if (m == 0) return run_steps(c, n_steps);
+    if (int rc = maybe_autotune(c)) return rc;
+    if (!c->grad.active && n_steps <= kGraphSteps) {
+        // the whole logged run as one recorded graph
+        if (int rc = launch_graph(c, n_steps, every)) return rc;
+        c->steps_done += n_steps;
+        return ACS_OK;
+    }
     if (enqueue_reduce(c, c->phi, c->log, c->stream) != cudaSuccess) return ACS_E_CUDA;
     int64_t done = 0;
     for (int64_t k = 1; k < m; ++k) {

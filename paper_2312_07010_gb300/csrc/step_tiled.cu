@@ -87,10 +87,22 @@ template cudaError_t launch_step_temporal<float>(int, int, int, const float*, fl
 template cudaError_t launch_step_temporal<double>(int, int, int, const double*, double*, const Geo&,
                                                   const Coef<double>&, int*, cudaStream_t);
 
+// Static choice for problems the autotuner does not time (below 2^20 unknowns).  The
+// tiled kernels give a CTA a whole tile (16 rows of 64 FP64 / 128 FP32 values, times
+// a run of planes in 3D), so a small grid makes few CTAs: FP64, bound by the FP64
+// pipe (1/64 of the FP32 rate), then runs on a fraction of the SMs, and a small FP32
+// grid pays the tile pipeline's fill for little work.  One thread per unknown spreads
+// those grids over every SM (measured per step, one-thread kernel against tiled:
+// 128^2 FP64 2.5 us / 11.8 us, 96^3 FP64 76 / 103 us, 256^2 FP32 1.5 / 2.2 us,
+// 384^2 FP32 2.3 / 2.4 us; from 512^2 and 96^3 FP32 the tiled kernels win).
+constexpr int64_t kSmallFp64 = int64_t(1) << 20;
+constexpr int64_t kSmallFp32 = int64_t(1) << 18;
+
 void resolve_auto_kernel(int dims, int dtype, int bc, const Geo& g, int* kernel, int* depth) {
     (void)bc;
     *depth = 1;
-    *kernel = tiled_supported(dims, dtype, g) ? ACS_KERNEL_TILED : ACS_KERNEL_NAIVE;
+    const bool small = g.total < (dtype == ACS_F64 ? kSmallFp64 : kSmallFp32);
+    *kernel = tiled_supported(dims, dtype, g) && !small ? ACS_KERNEL_TILED : ACS_KERNEL_NAIVE;
 }
 
 }  // namespace acs

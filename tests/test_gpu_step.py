@@ -73,13 +73,20 @@ def test_fp32_parity_200_steps(acs, shape, bc):
     assert float(np.abs(got).max()) <= 1.0
 
 
+@pytest.mark.parametrize("kernel", ["naive", "tiled"])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
 @pytest.mark.parametrize("shape", [(9,), (5, 7), (33, 65), (7, 6, 5), (40, 33, 20), (9, 20, 136), (64, 64, 64),
                                    (1, 3, 8)], ids=str)
-def test_energy_and_maxnorm_parity(acs, shape, bc, dtype):
+def test_energy_and_maxnorm_parity(acs, shape, bc, dtype, kernel):
+    """Both reductions: the row-per-block pass (with the naive kernel) and the streamed
+    pass of the tiled kernels (where the shape has one)."""
     h, eps, dt, phi0 = _problem(shape, bc, 41 + len(shape) + bc)
     s = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    try:
+        s.set_kernel(acs.ACS_KERNEL_TILED if kernel == "tiled" else acs.ACS_KERNEL_NAIVE)
+    except acs.AcsError:
+        pytest.skip("no tiled kernel for this shape")
     s.set_state(phi0)
     s.step(3)
     state = s.numpy().astype(np.float64)
