@@ -2,6 +2,8 @@
 // reduction kernels (energy / maximum norm, adjoint gradient sums).
 #pragma once
 
+#include <climits>
+
 #include "acs_device.cuh"
 
 namespace acs {
@@ -34,18 +36,199 @@ __device__ __forceinline__ CSum shfl_down(CSum v, int off) {
     return CSum{__shfl_down_sync(0xffffffffu, v.s, off), __shfl_down_sync(0xffffffffu, v.c, off)};
 }
 
-// Sum a CSum over the threads of a block (<= 1024, any shape) in a fixed order; the
-// result is valid in thread 0.  `scratch` needs 32 entries.
-__device__ __forceinline__ CSum block_csum(CSum v, CSum* scratch) {
-    for (int off = 16; off > 0; off >>= 1) v = cmerge(v, shfl_down(v, off));
-    // linear thread index, so 2D blocks (32 x k) reduce correctly too
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nwarps = (int)((blockDim.x * blockDim.y + 31) >> 5);
-    if ((tid & 31) == 0) scratch[tid >> 5] = v;
+// ---------------------------------------------------------------- exact combination
+// FP64 arithmetic on this GPU has a small fraction of the FP32 issue rate and a long
+// dependent latency, so trees of compensated FP64 merges (about six dependent
+// operations per level) made a block's final combination cost more than its data
+// (15 us for 16 K values).  Partial sums are combined exactly in 128-bit two's-
+// complement fixed point instead: with E the largest biased exponent among the
+// values, the unit is 2^(E - 1122), so every value is below 2^100 units and up to
+// 2^26 of them sum without overflow; bits below 2^-99 of the largest value are
+// dropped (truncated toward zero).  Integer addition is associative, so the result
+// does not depend on the order of the tree, and the tree runs on the integer pipes.
+// All block-level helpers below take blocks whose size is a multiple of 32 and must
+// be called by every thread of the block.
+
+struct Fix {
+    unsigned long long lo;
+    long long hi;
+};
+
+constexpr int kFixShift = 47;  // the largest value is below 2^(53 + kFixShift) units
+constexpr int kFixUnit = 1075 + kFixShift;
+
+__device__ __forceinline__ int dexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7ff); }
+
+__device__ __forceinline__ Fix fix_neg(Fix x) {
+    x.lo = ~x.lo + 1ull;
+    x.hi = ~x.hi + (x.lo == 0ull ? 1ll : 0ll);
+    return x;
+}
+
+// v in units of 2^(E - kFixUnit), truncated toward zero; exact when v is a multiple of
+// the unit.  Requires dexp(v) <= E + 27 (|v| below 2^127 units).
+__device__ __forceinline__ Fix fix_of(double v, int E) {
+    const long long bits = __double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    unsigned long long m = (unsigned long long)bits & 0x000fffffffffffffull;
+    if (e != 0) m |= 0x0010000000000000ull;
+    const int sh = (e == 0 ? 1 : e) - E + kFixShift;  // v = m 2^(e - 1075) = m 2^sh units
+    Fix r{0ull, 0ll};
+    if (m == 0ull || sh <= -53) return r;
+    if (sh < 0) {
+        r.lo = m >> (-sh);
+    } else if (sh == 0) {
+        r.lo = m;
+    } else if (sh < 64) {
+        r.lo = m << sh;
+        r.hi = (long long)(m >> (64 - sh));
+    } else {
+        r.hi = (long long)(m << (sh - 64));
+    }
+    return bits < 0 ? fix_neg(r) : r;
+}
+
+__device__ __forceinline__ Fix fix_add(Fix a, Fix b) {
+    Fix r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ll : 0ll);
+    return r;
+}
+
+__device__ __forceinline__ Fix fix_shfl_down(Fix a, int off) {
+    return Fix{__shfl_down_sync(0xffffffffu, a.lo, off), __shfl_down_sync(0xffffffffu, a.hi, off)};
+}
+
+// 2^k as a double, -1074 <= k <= 1023 (below 2^-1022 as an exact product of two)
+__device__ __forceinline__ double pow2i(int k) {
+    if (k >= -1022) return __longlong_as_double((long long)(k + 1023) << 52);
+    return __longlong_as_double((long long)(k + 200 + 1023) << 52) * __longlong_as_double((long long)(823) << 52);
+}
+
+// x (in whole units) as a double: the magnitude's two 64-bit halves combined by one
+// fused multiply-add (at most two roundings).
+__device__ __forceinline__ double fix_units(Fix x) {
+    const bool neg = x.hi < 0;
+    if (neg) x = fix_neg(x);
+    const double d = __fma_rn((double)(unsigned long long)x.hi, 18446744073709551616.0, (double)x.lo);
+    return neg ? -d : d;
+}
+
+// The unevaluated pair (s, c) of x units of 2^(E - kFixUnit): s = x rounded, c the
+// exact integer remainder x - s rounded, so s + c carries about 106 bits.
+__device__ __forceinline__ CSum fix_to_csum(Fix x, int E) {
+    const double s_units = fix_units(x);
+    const Fix rem = fix_add(x, fix_neg(fix_of(s_units, kFixUnit)));  // s_units is an integer
+    const double c_units = fix_units(rem);
+    const double scale = pow2i(E - kFixUnit);
+    return CSum{s_units * scale, c_units * scale};
+}
+
+__device__ __forceinline__ int block_tid() { return threadIdx.y * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int block_nwarps() { return (int)((blockDim.x * blockDim.y + 31) >> 5); }
+
+// Block-wide maximum (op 0) or bitwise or (op 1) of an int, returned to every thread.
+template <int OP>
+__device__ __forceinline__ int block_int_reduce(int v) {
+    __shared__ int sw[32];
+    __shared__ int res;
+    v = OP == 0 ? __reduce_max_sync(0xffffffffu, v) : (int)__reduce_or_sync(0xffffffffu, (unsigned)v);
+    const int tid = block_tid();
+    if ((tid & 31) == 0) sw[tid >> 5] = v;
     __syncthreads();
-    if (tid == 0)
-        for (int w = 1; w < nwarps; ++w) v = cmerge(v, scratch[w]);
+    if (tid < 32) {
+        int w = tid < block_nwarps() ? sw[tid] : (OP == 0 ? INT_MIN : 0);
+        w = OP == 0 ? __reduce_max_sync(0xffffffffu, w) : (int)__reduce_or_sync(0xffffffffu, (unsigned)w);
+        if (tid == 0) res = w;
+    }
+    __syncthreads();
+    return res;
+}
+
+// Block-wide sum of one Fix per thread (valid in thread 0).
+__device__ __forceinline__ Fix block_fix_sum(Fix v) {
+    __shared__ Fix sw[32];
+    for (int off = 16; off > 0; off >>= 1) v = fix_add(v, fix_shfl_down(v, off));
+    const int tid = block_tid();
+    if ((tid & 31) == 0) sw[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        Fix w = tid < block_nwarps() ? sw[tid] : Fix{0ull, 0ll};
+        for (int off = 16; off > 0; off >>= 1) w = fix_add(w, fix_shfl_down(w, off));
+        v = w;
+    }
+    __syncthreads();
     return v;
+}
+
+// non-finite classes of a double: 1 = NaN, 2 = +Inf, 4 = -Inf, 0 = finite
+__device__ __forceinline__ int nonfinite_bits(double v) {
+    if (v != v) return 1;
+    if (dexp(v) != 0x7ff) return 0;
+    return v > 0.0 ? 2 : 4;
+}
+__device__ __forceinline__ CSum nonfinite_sum(int bits) {
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    if ((bits & 1) || (bits & 6) == 6) return CSum{inf - inf, 0.0};
+    return CSum{(bits & 2) ? inf : -inf, 0.0};
+}
+
+// Exact sum over the block of the pairs get(i), i = tid, tid + nthreads, ... < n
+// (n <= 2^25); the result is valid in thread 0.  Non-finite inputs give NaN if any
+// is NaN or both infinities occur, else that infinity.
+template <typename Get>
+__device__ __forceinline__ CSum block_sum_pairs(int n, Get get) {
+    const int tid = block_tid(), nt = (int)(blockDim.x * blockDim.y);
+    int key = 0;
+    for (int i = tid; i < n; i += nt) {
+        const CSum p = get(i);
+        key = max(key, max(dexp(p.s), dexp(p.c)));
+    }
+    const int E = block_int_reduce<0>(key);
+    if (E == 0x7ff) {
+        int bits = 0;
+        for (int i = tid; i < n; i += nt) {
+            const CSum p = get(i);
+            bits |= nonfinite_bits(p.s) | nonfinite_bits(p.c);
+        }
+        return nonfinite_sum(block_int_reduce<1>(bits));
+    }
+    Fix f{0ull, 0ll};
+    for (int i = tid; i < n; i += nt) {
+        const CSum p = get(i);
+        f = fix_add(f, fix_add(fix_of(p.s, E), fix_of(p.c, E)));
+    }
+    return fix_to_csum(block_fix_sum(f), E);
+}
+
+// Exact sum of one CSum per thread over a block (result valid in thread 0).
+__device__ __forceinline__ CSum block_csum(CSum v) {
+    const int E = block_int_reduce<0>(max(dexp(v.s), dexp(v.c)));
+    if (E == 0x7ff) return nonfinite_sum(block_int_reduce<1>(nonfinite_bits(v.s) | nonfinite_bits(v.c)));
+    return fix_to_csum(block_fix_sum(fix_add(fix_of(v.s, E), fix_of(v.c, E))), E);
+}
+
+// maximum of non-negative doubles (NaN wins), on their bit patterns
+__device__ __forceinline__ double max_bits(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+
+// Block-wide maximum of non-negative doubles (NaN wins: as integers the bit patterns
+// of non-negative values, +Inf and positive NaN are ordered); valid in thread 0.
+__device__ __forceinline__ double block_max_nonneg(double v) {
+    __shared__ long long sw[32];
+    long long b = __double_as_longlong(v);
+    for (int off = 16; off > 0; off >>= 1) b = max(b, __shfl_down_sync(0xffffffffu, b, off));
+    const int tid = block_tid();
+    if ((tid & 31) == 0) sw[tid >> 5] = b;
+    __syncthreads();
+    if (tid < 32) {
+        long long w = tid < block_nwarps() ? sw[tid] : 0ll;
+        for (int off = 16; off > 0; off >>= 1) w = max(w, __shfl_down_sync(0xffffffffu, w, off));
+        b = w;
+    }
+    __syncthreads();
+    return __longlong_as_double(b);
 }
 
 // ---------------------------------------------------------------- FP32 states

@@ -102,21 +102,16 @@ __global__ void __launch_bounds__(256) k_adjoint(const T* __restrict__ phin, con
             cadd(ge, (double)mu * ((double)sphi - 2.0 * D * (double)p));
         }
     }
-    __shared__ CSum scratch[32];
-    ge = block_csum(ge, scratch);
+    ge = block_csum(ge);
     if (threadIdx.x == 0) part[blockIdx.x] = cmerge(part[blockIdx.x], ge);
 }
 
 // acc += the partials of a segment: steps x nparts entries, in a fixed order.
 __global__ void k_adjoint_finish(const CSum* part, int steps, int stride, int nparts, CSum* acc) {
-    CSum s{0.0, 0.0};
-    const int total = steps * nparts;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const CSum s = block_sum_pairs(steps * nparts, [&](int i) {
         const int st = i / nparts, b = i - st * nparts;
-        s = cmerge(s, part[(size_t)st * stride + b]);
-    }
-    __shared__ CSum scratch[32];
-    s = block_csum(s, scratch);
+        return part[(size_t)st * stride + b];
+    });
     if (threadIdx.x == 0) acc[0] = cmerge(acc[0], s);
 }
 
@@ -186,8 +181,7 @@ __global__ void __launch_bounds__(256) k_adjoint2d(const T* __restrict__ phin, c
         cadd(ge, (double)tile_sum);
         __syncthreads();
     }
-    __shared__ CSum scratch[32];
-    ge = block_csum(ge, scratch);
+    ge = block_csum(ge);
     if (threadIdx.x == 0) part[blockIdx.x] = cmerge(part[blockIdx.x], ge);
 }
 

@@ -93,49 +93,24 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g
         cadd(link, dl);
     }
     // the bulk terms above are (p^2 - 1)^2; the 1/4 is applied at the end (exact)
-    for (int off = 16; off > 0; off >>= 1) {
-        bulk = cmerge(bulk, shfl_down(bulk, off));
-        link = cmerge(link, shfl_down(link, off));
-        mxd = nmax(mxd, __shfl_down_sync(0xffffffffu, mxd, off));
-    }
-    __shared__ CSum sb[8], sl[8];
-    __shared__ double sm[8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sb[warp] = bulk; sl[warp] = link; sm[warp] = mxd; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        CSum B = sb[0], L = sl[0];
-        double M = sm[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { B = cmerge(B, sb[w]); L = cmerge(L, sl[w]); M = nmax(M, sm[w]); }
-        part[blockIdx.x] = RedPartial{B.s, B.c, L.s, L.c, M, 0.0, 0.0, 0.0};
-    }
+    const CSum B = block_csum(bulk);
+    const CSum L = block_csum(link);
+    const double M = block_max_nonneg(mxd);
+    if (threadIdx.x == 0) part[blockIdx.x] = RedPartial{B.s, B.c, L.s, L.c, M, 0.0, 0.0, 0.0};
 }
 
 __global__ void k_reduce_finish(const RedPartial* part, int nparts, double hd, double link_scale,
                                 double* out2) {
-    CSum B{0.0, 0.0}, L{0.0, 0.0};
-    double M = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        B = cmerge(B, CSum{part[i].bulk_s, part[i].bulk_c});
-        L = cmerge(L, CSum{part[i].link_s, part[i].link_c});
-        M = nmax(M, part[i].mx);
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        B = cmerge(B, shfl_down(B, off));
-        L = cmerge(L, shfl_down(L, off));
-        M = nmax(M, __shfl_down_sync(0xffffffffu, M, off));
-    }
-    __shared__ CSum sb[8], sl[8];
-    __shared__ double sm[8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sb[warp] = B; sl[warp] = L; sm[warp] = M; }
-    __syncthreads();
+    const CSum B = block_sum_pairs(nparts, [&](int i) { return CSum{part[i].bulk_s, part[i].bulk_c}; });
+    const CSum L = block_sum_pairs(nparts, [&](int i) { return CSum{part[i].link_s, part[i].link_c}; });
+    double m = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) m = max_bits(m, part[i].mx);
+    const double M = block_max_nonneg(m);
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { sb[0] = cmerge(sb[0], sb[w]); sl[0] = cmerge(sl[0], sl[w]); sm[0] = nmax(sm[0], sm[w]); }
-        const double bulk = sb[0].s + sb[0].c;
-        const double links = sl[0].s + sl[0].c;
+        const double bulk = B.s + B.c;
+        const double links = L.s + L.c;
         out2[0] = hd * (0.25 * bulk + link_scale * links);
-        out2[1] = sm[0];
+        out2[1] = M;
     }
 }
 
@@ -203,16 +178,12 @@ __global__ void __launch_bounds__(256) k_phase_sum(const T* __restrict__ src, in
     } else {
         cadd(sum, d);
     }
-    __shared__ CSum scratch[32];
-    sum = block_csum(sum, scratch);
+    sum = block_csum(sum);
     if (threadIdx.x == 0) part[blockIdx.x] = sum;
 }
 
 __global__ void k_phase_finish(const CSum* part, int nparts, int64_t n, double hd, double* out) {
-    CSum s{0.0, 0.0};
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s = cmerge(s, part[i]);
-    __shared__ CSum scratch[32];
-    s = block_csum(s, scratch);
+    const CSum s = block_sum_pairs(nparts, [&](int i) { return part[i]; });
     if (threadIdx.x == 0) out[0] = hd * 0.5 * ((double)n + (s.s + s.c));
 }
 

@@ -112,25 +112,10 @@ struct EnergyAcc<double> {
 template <typename T>
 __device__ __forceinline__ void energy_block_write(EnergyAcc<T>& acc, RedPartial* out) {
     acc.finish();
-    CSum b{acc.db, 0.0}, l{acc.dl, 0.0};
-    double m = acc.mx;
-    for (int off = 16; off > 0; off >>= 1) {
-        b = cmerge(b, shfl_down(b, off));
-        l = cmerge(l, shfl_down(l, off));
-        m = nmax(m, __shfl_down_sync(0xffffffffu, m, off));
-    }
-    __shared__ CSum sb[32], sl[32];
-    __shared__ double sm[32];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-    __syncthreads();
-    if (lane == 0) { sb[warp] = b; sl[warp] = l; sm[warp] = m; }
-    __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < nw; ++w) { b = cmerge(b, sb[w]); l = cmerge(l, sl[w]); m = nmax(m, sm[w]); }
-        *out = RedPartial{b.s, b.c, l.s, l.c, m, 0.0, 0.0, 0.0};
-    }
+    const CSum b = block_csum(CSum{acc.db, 0.0});
+    const CSum l = block_csum(CSum{acc.dl, 0.0});
+    const double m = block_max_nonneg(acc.mx);
+    if (block_tid() == 0) *out = RedPartial{b.s, b.c, l.s, l.c, m, 0.0, 0.0, 0.0};
 }
 
 // Tile variants offered to the autotuner: (rows per thread, ring slots).

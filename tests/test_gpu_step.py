@@ -96,6 +96,54 @@ def test_energy_and_maxnorm_parity(acs, shape, bc, dtype, kernel):
     assert M == oracle.maxnorm(state)
 
 
+def _energy_exact(phi, eps, h):
+    """E_h of a Neumann state in exact rational arithmetic: h^d [1/4 sum (p^2 - 1)^2 +
+    eps^2 / 2 sum over interior links ((q - p) / h)^2] (Theorem 3 with the quadratic form
+    written as link sums), rounded once at the end."""
+    from fractions import Fraction as F
+    P = np.vectorize(F, otypes=[object])(phi)
+    h_, e_ = F(h), F(eps)
+    bulk = sum(((P * P - 1) ** 2).ravel(), F(0))
+    links = F(0)
+    for ax in range(phi.ndim):
+        d = np.diff(P, axis=ax)
+        links += sum((d * d).ravel(), F(0))
+    return float(h_ ** phi.ndim * (bulk / 4 + e_ * e_ / 2 * links / (h_ * h_)))
+
+
+@pytest.mark.parametrize("kernel", ["naive", "tiled"])
+@pytest.mark.parametrize("case", ["near_uniform", "wide_range", "inf"])
+def test_energy_extreme_states(acs, case, kernel):
+    """The partial sums are combined exactly in fixed point scaled by their largest
+    exponent: a total of order 1e-20 (one point 1e-9 below the uniform state 1), values
+    spanning 300 decades with random signs, and an infinite entry.  Reference: the
+    definition in exact rational arithmetic."""
+    shape = (12, 10, 8)
+    h, eps = 1 / 12, 0.02
+    dt = 0.5 * acs.dt_max(3, eps, h)[0]
+    rng = np.random.default_rng(11)
+    if case == "near_uniform":
+        phi = np.ones(shape)
+        phi[7, 3, 5] = 1 - 1e-9
+    elif case == "wide_range":
+        phi = np.sign(rng.uniform(-1, 1, shape)) * 10.0 ** rng.uniform(-300, 2, shape)
+    else:
+        phi = rng.uniform(-1, 1, shape)
+        phi[3, 4, 5] = np.inf
+    s = acs.AllenCahn(shape, eps, dt, h, BC_NEUMANN, "f64")
+    s.set_kernel(acs.ACS_KERNEL_TILED if kernel == "tiled" else acs.ACS_KERNEL_NAIVE)
+    s.set_state(phi)
+    E = s.energy(allow_nonfinite=True)
+    M = s.maxnorm(allow_nonfinite=True)
+    if case == "inf":
+        assert not np.isfinite(E) and M == np.inf
+        return
+    ref = _energy_exact(phi, eps, h)
+    assert ref > 0
+    assert E == pytest.approx(ref, rel=1e-12, abs=0)
+    assert M == np.abs(phi).max()
+
+
 def test_cfg1_full_run(acs):
     """2D 128^2 periodic, FP64, 1000 steps, E_h and max-norm every 10 steps."""
     w = cfg1()
