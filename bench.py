@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kernel", type=int, default=0, help="ACS_KERNEL_* (0 = auto)")
     ap.add_argument("--depth", type=int, default=1)
+    ap.add_argument("--variant", type=int, default=-1, help="tile variant of the tiled kernel (-1 = tuned)")
+    ap.add_argument("--chunk", type=int, default=0, help="planes per CTA with --variant (0 = automatic)")
     ap.add_argument("--profile", action="store_true",
                     help="only set up the 512^3 workload and run --steps time steps (for ncu captures)")
     ap.add_argument("--profile-lb", action="store_true",
@@ -261,6 +263,8 @@ def main():
         s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32", stream=stream)
     if args.kernel:
         s.set_kernel(args.kernel, args.depth)
+    if args.variant >= 0:
+        P.check(P.lib().acs_set_variant(s.ctx, args.variant, args.chunk), "acs_set_variant")
     s.set_state(phi0_dev)
     s.step(2)  # the first step of an auto-kernel context runs the autotuner
     kernel, depth = s.get_kernel()

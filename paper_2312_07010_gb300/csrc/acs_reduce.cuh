@@ -173,39 +173,66 @@ __device__ __forceinline__ CSum nonfinite_sum(int bits) {
     return CSum{(bits & 2) ? inf : -inf, 0.0};
 }
 
+// arithmetic shift right of a two's-complement 128-bit value (truncates toward -inf)
+__device__ __forceinline__ Fix fix_shr(Fix x, int k) {
+    if (k <= 0) return x;
+    if (k >= 127) return Fix{x.hi < 0 ? ~0ull : 0ull, x.hi < 0 ? -1ll : 0ll};
+    if (k >= 64) return Fix{(unsigned long long)(x.hi >> (k - 64)), x.hi < 0 ? -1ll : 0ll};
+    return Fix{(x.lo >> k) | ((unsigned long long)x.hi << (64 - k)), x.hi >> k};
+}
+
+// A running exact sum whose unit follows the largest exponent seen so far: a larger
+// exponent rescales the sum (a right shift, dropping bits below the new unit), so one
+// pass over the values suffices.  Non-finite values are recorded as classes.
+struct FixAcc {
+    Fix f{0ull, 0ll};
+    int E = 0;
+    int bad = 0;
+    __device__ __forceinline__ void add(double v) {
+        const int e = dexp(v);
+        if (e == 0x7ff) {
+            bad |= nonfinite_bits(v);
+            return;
+        }
+        if (e > E) {
+            f = fix_shr(f, e - E);
+            E = e;
+        }
+        f = fix_add(f, fix_of(v, E));
+    }
+};
+
+// Combine one FixAcc per thread over the block; the (s, c) result is valid in thread
+// 0.  Non-finite inputs give NaN if any is NaN or both infinities occur, else that
+// infinity.  At most 2^26 values in all.
+__device__ __forceinline__ CSum block_fixacc(const FixAcc& a) {
+    const int bad = block_int_reduce<1>(a.bad);
+    if (bad) return nonfinite_sum(bad);
+    const int E = block_int_reduce<0>(a.E);
+    return fix_to_csum(block_fix_sum(fix_shr(a.f, E - a.E)), E);
+}
+
 // Exact sum over the block of the pairs get(i), i = tid, tid + nthreads, ... < n
-// (n <= 2^25); the result is valid in thread 0.  Non-finite inputs give NaN if any
-// is NaN or both infinities occur, else that infinity.
+// (n <= 2^25), in one pass; the result is valid in thread 0.
 template <typename Get>
 __device__ __forceinline__ CSum block_sum_pairs(int n, Get get) {
     const int tid = block_tid(), nt = (int)(blockDim.x * blockDim.y);
-    int key = 0;
+    FixAcc a;
+#pragma unroll 4
     for (int i = tid; i < n; i += nt) {
         const CSum p = get(i);
-        key = max(key, max(dexp(p.s), dexp(p.c)));
+        a.add(p.s);
+        a.add(p.c);
     }
-    const int E = block_int_reduce<0>(key);
-    if (E == 0x7ff) {
-        int bits = 0;
-        for (int i = tid; i < n; i += nt) {
-            const CSum p = get(i);
-            bits |= nonfinite_bits(p.s) | nonfinite_bits(p.c);
-        }
-        return nonfinite_sum(block_int_reduce<1>(bits));
-    }
-    Fix f{0ull, 0ll};
-    for (int i = tid; i < n; i += nt) {
-        const CSum p = get(i);
-        f = fix_add(f, fix_add(fix_of(p.s, E), fix_of(p.c, E)));
-    }
-    return fix_to_csum(block_fix_sum(f), E);
+    return block_fixacc(a);
 }
 
 // Exact sum of one CSum per thread over a block (result valid in thread 0).
 __device__ __forceinline__ CSum block_csum(CSum v) {
-    const int E = block_int_reduce<0>(max(dexp(v.s), dexp(v.c)));
-    if (E == 0x7ff) return nonfinite_sum(block_int_reduce<1>(nonfinite_bits(v.s) | nonfinite_bits(v.c)));
-    return fix_to_csum(block_fix_sum(fix_add(fix_of(v.s, E), fix_of(v.c, E))), E);
+    FixAcc a;
+    a.add(v.s);
+    a.add(v.c);
+    return block_fixacc(a);
 }
 
 // maximum of non-negative doubles (NaN wins), on their bit patterns

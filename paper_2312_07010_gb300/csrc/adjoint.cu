@@ -199,19 +199,31 @@ __device__ __forceinline__ double adj_mu(double l, double q, const Coef<double>&
     return l * r;
 }
 
-// Sum of one value per thread over a block of 32 x 8 threads: warp shuffles in T,
-// the eight warp sums folded in FP64 by thread (0, 0), where the result is valid.
-template <typename T>
-__device__ __forceinline__ double block_sum_t(T v) {
-    __shared__ T ws[8];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (threadIdx.x == 0) ws[threadIdx.y] = v;
+// Sum of one value per thread over a block of 32 x 8 threads, valid in thread (0, 0).
+// FP32: unevaluated float pairs (TwoSum) through the warp shuffles and the eight warp
+// sums, about 2^-44 relative, returned as an exact double pair -- no FP64 arithmetic,
+// whose dependent latency on this GPU would dominate the step's tail.  FP64: the
+// exact fixed-point block sum.
+__device__ __forceinline__ CSum cta_sum(float v) {
+    F2 a{v, 0.0f};
+    for (int off = 16; off > 0; off >>= 1) {
+        const float bh = __shfl_down_sync(0xffffffffu, a.hi, off);
+        const float bl = __shfl_down_sync(0xffffffffu, a.lo, off);
+        const F2 t = two_sum(a.hi, bh);
+        a = F2{t.hi, (a.lo + bl) + t.lo};
+    }
+    __shared__ F2 ws[8];
+    if (threadIdx.x == 0) ws[threadIdx.y] = a;
     __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int w = 0; w < 8; ++w) t += (double)ws[w];
-    return t;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        for (int w = 1; w < 8; ++w) {
+            const F2 t = two_sum(a.hi, ws[w].hi);
+            a = F2{t.hi, (a.lo + ws[w].lo) + t.lo};
+        }
+    }
+    return CSum{(double)a.hi, (double)a.lo};
 }
+__device__ __forceinline__ CSum cta_sum(double v) { return block_csum(CSum{v, 0.0}); }
 
 // 2D adjoint step streamed through TMA (rows a multiple of 16 bytes).  A CTA owns a
 // column of TX unknowns and a run of 16-row blocks; per block one thread loads the
@@ -386,14 +398,10 @@ __global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ C
             mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
         }
     }
-    // the CTA's share of the step, added to its FP64 running sum over the sweep
-    const double t = block_sum_t<T>(tile_sum);
+    // the CTA's share of this step, added to its running sum over the sweep
+    const CSum t = cta_sum(tile_sum);
     const int cta = blockIdx.y * gridDim.x + blockIdx.x;
-    if (tid == 0) {
-        CSum ge{0.0, 0.0};
-        cadd(ge, t);
-        part[cta] = cmerge(part[cta], ge);
-    }
+    if (tid == 0) part[cta] = cmerge(part[cta], t);
 }
 
 // One adjoint step adding its per-block eps^2 partials into `part` (kMaxRedBlocks
@@ -617,7 +625,7 @@ ACS_API int acs_grad(acs_ctx* c, const void* d_dL_dphiT, void* d_dL_dphi0, doubl
     // The whole sweep, recorded once per (N, every): per segment (last first)
     // recompute its states from the checkpoint, then step the adjoint back through
     // them.  Each adjoint launch adds its per-CTA eps^2 partials into part[cta]
-    // (always the same CTA order), folded once at the end: deterministic.
+    // (always the same CTA order), combined exactly once at the end: deterministic.
     auto sweep = [&](cudaStream_t s) -> bool {
         char* a = A;
         char* b = B;
@@ -638,12 +646,13 @@ ACS_API int acs_grad(acs_ctx* c, const void* d_dL_dphiT, void* d_dL_dphi0, doubl
                 const char* pk = k == 0 ? ck : G.buf + L.seg + L.sb * (size_t)(k - 1);
                 const char* pk1 = G.buf + L.seg + L.sb * (size_t)k;
                 cudaError_t e;
+                CSum* row = part;
                 if (v.dtype == ACS_F32)
                     e = launch_adjoint<float>(v.dims, v.bc, (const float*)pk, (const float*)pk1, (const float*)a,
-                                              (float*)b, v.g, v.cf, part, &nparts, v.err, s);
+                                              (float*)b, v.g, v.cf, row, &nparts, v.err, s);
                 else
                     e = launch_adjoint<double>(v.dims, v.bc, (const double*)pk, (const double*)pk1,
-                                               (const double*)a, (double*)b, v.g, v.cd, part, &nparts, v.err, s);
+                                               (const double*)a, (double*)b, v.g, v.cd, row, &nparts, v.err, s);
                 if (e != cudaSuccess) return false;
                 std::swap(a, b);
             }

@@ -101,10 +101,19 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g
 
 __global__ void k_reduce_finish(const RedPartial* part, int nparts, double hd, double link_scale,
                                 double* out2) {
-    const CSum B = block_sum_pairs(nparts, [&](int i) { return CSum{part[i].bulk_s, part[i].bulk_c}; });
-    const CSum L = block_sum_pairs(nparts, [&](int i) { return CSum{part[i].link_s, part[i].link_c}; });
+    FixAcc b, l;
     double m = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) m = max_bits(m, part[i].mx);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const RedPartial p = part[i];
+        b.add(p.bulk_s);
+        b.add(p.bulk_c);
+        l.add(p.link_s);
+        l.add(p.link_c);
+        m = max_bits(m, p.mx);
+    }
+    const CSum B = block_fixacc(b);
+    const CSum L = block_fixacc(l);
     const double M = block_max_nonneg(m);
     if (threadIdx.x == 0) {
         const double bulk = B.s + B.c;
