@@ -171,6 +171,39 @@ def cpu_oracle_sample(budget_s: float = 12.0):
                       f"(plain C, OpenMP over points), {el:.1f} s"}
 
 
+def oracle_cpu_timing():
+    """The FP64 oracle's FD step on the host cores, single-threaded and on all cores, for
+    the 128^2 periodic (all 1000 steps), 4096^2 Dirichlet (2 steps) and 512^3 Neumann (1
+    step) workloads: updates per second, with the CPU model and core count."""
+    import oracle
+    from workloads import cfg1, cfg2, cfg3
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    cores = oracle.numthreads()
+    res = {"cpu_model": model, "nproc": os.cpu_count(), "threads_all": cores, "unit": "GLUPS"}
+    for name, w, steps in (("cfg1_128sq_periodic_1000_steps", cfg1(), 1000),
+                           ("cfg3_4096sq_dirichlet_2_steps", cfg3("f64"), 2),
+                           ("cfg2_512cubed_neumann_1_step", cfg2("f64"), 1)):
+        phi0 = w.phi0()
+        oracle.step_fd(phi0, w.eps, w.dt, w.h, w.bc)  # untimed: first touch of the arrays
+        row = {}
+        for label, t in (("single_thread", 1), ("all_threads", cores)):
+            oracle.set_threads(t)
+            t0 = time.perf_counter()
+            oracle.run_fd(phi0, w.eps, w.dt, w.h, w.bc, steps)
+            row[label] = w.numel * steps / (time.perf_counter() - t0) / 1e9
+        res[name] = row
+    oracle.set_threads(cores)
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -402,6 +435,8 @@ def main():
         line["extra"] = extras(P, args)
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample()
+        if not args.no_extras:
+            line.setdefault("extra", {})["oracle_cpu"] = oracle_cpu_timing()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:
@@ -502,6 +537,24 @@ def extras(P, args):
     from workloads import cfg1, cfg2, cfg3, cfg5, tanh_disc
     out = {}
     peak, _ = _peaks()
+    # the E_h / max-norm pass on the 512^3 FP32 state: it reads the state once (4 B per
+    # unknown) and forms every term exactly, so it is bound by FP32 issue, not HBM
+    w2 = cfg2("f32")
+    s = P.AllenCahn(w2.n, w2.eps, w2.dt, w2.h, w2.bc, "f32")
+    s.set_state(torch.from_numpy(w2.phi0().astype(np.float32)).cuda())
+    s.step(2)
+    d2 = torch.empty(2, dtype=torch.float64, device="cuda")
+
+    def observe():
+        P.lib().acs_observe_async(s.ctx, ctypes.c_void_p(d2.data_ptr()))
+    ms = _time(observe, 10)
+    out["energy_pass_512cubed_f32"] = {"us": ms * 1e3, "alg_bytes": w2.numel * 4,
+                                       "achieved_gbs": w2.numel * 4 / (ms * 1e-3) / 1e9,
+                                       "hbm_frac": w2.numel * 4 / (ms * 1e-3) / 1e9 / peak,
+                                       "bound": "FP32 issue (exact terms: about 90 operations per unknown)"}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
     # FP64 on the 512^3 workload (fewer steps)
     for name, w, nsteps in (("cfg2_fp64_512cubed", cfg2("f64"), 20), ("cfg3_fp32_4096sq", cfg3("f32"), 200),
                             ("cfg3_fp64_4096sq", cfg3("f64"), 50), ("cfg1_fp64_128sq", cfg1(), 1000)):
@@ -556,7 +609,8 @@ def extras(P, args):
     out["cfg4_batched_256"] = {"glups": units / (ms_b * 1e-3) / 1e9, "ms": ms_b, "instances": len(inst),
                                "unknowns": sum(i.n * i.n for i in inst), "steps": BATCH_STEPS,
                                "sequential_single_glups": units / (ms_s * 1e-3) / 1e9, "sequential_ms": ms_s,
-                               "speedup_vs_sequential": ms_s / ms_b, "max_abs_phi": float(np.max(M))}
+                               "speedup_vs_sequential": ms_s / ms_b, "max_abs_phi": float(np.max(M)),
+                               "hbm_frac_effective": units / (ms_b * 1e-3) * 8 / (peak * 1e9)}
     del singles, b
     torch.cuda.empty_cache()
     # adjoint: 1024^2 periodic, FP32, 500 steps, checkpoints every 50

@@ -22,12 +22,15 @@ def acs():
     return P
 
 
+# odd rows take the one-value-per-thread kernels, rows of a multiple of four values the
+# vectorised ones
 SHAPES = {1: (301,), 2: (37, 45), 3: (13, 17, 19)}
+VSHAPES = {1: (300,), 2: (37, 44), 3: (13, 17, 20)}
 
 
-def _problem(dims, bc, seed=0):
+def _problem(dims, bc, seed=0, vec=False):
     rng = np.random.default_rng(seed + 10 * dims + bc)
-    shape = SHAPES[dims]
+    shape = (VSHAPES if vec else SHAPES)[dims]
     n = shape[-1]
     h = 1.0 / (n + 1) if bc == 2 else 1.0 / n
     eps = 0.03
@@ -36,10 +39,11 @@ def _problem(dims, bc, seed=0):
     return rng.uniform(-1, 1, size=shape), eps, dt, h
 
 
+@pytest.mark.parametrize("vec", [False, True], ids=["scalar", "vector"])
 @pytest.mark.parametrize("dims", [1, 2, 3])
 @pytest.mark.parametrize("bc", [0, 1, 2])
-def test_lb_fp64_matches_oracle_lb(acs, dims, bc):
-    phi0, eps, dt, h = _problem(dims, bc)
+def test_lb_fp64_matches_oracle_lb(acs, dims, bc, vec):
+    phi0, eps, dt, h = _problem(dims, bc, vec=vec)
     s = acs.AllenCahn(phi0.shape, eps, dt, h, bc, "f64")
     s.use_lb_form()
     s.set_state(phi0)
@@ -51,11 +55,12 @@ def test_lb_fp64_matches_oracle_lb(acs, dims, bc):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("vec", [False, True], ids=["scalar", "vector"])
 @pytest.mark.parametrize("dims", [2, 3])
 @pytest.mark.parametrize("omega1", [0.0, 0.05, 0.11])
-def test_lb_equals_fd_to_rounding(acs, dims, omega1):
+def test_lb_equals_fd_to_rounding(acs, dims, omega1, vec):
     bc = 1
-    phi0, eps, dt, h = _problem(dims, bc, seed=3)
+    phi0, eps, dt, h = _problem(dims, bc, seed=3, vec=vec)
     a = acs.AllenCahn(phi0.shape, eps, dt, h, bc, "f64")
     a.use_lb_form(omega1)
     b = acs.AllenCahn(phi0.shape, eps, dt, h, bc, "f64")
@@ -67,8 +72,9 @@ def test_lb_equals_fd_to_rounding(acs, dims, omega1):
     assert np.abs(x - y).max() <= 1e-13
 
 
-def test_lb_fp32_close_to_fd(acs):
-    phi0, eps, dt, h = _problem(3, 0, seed=5)
+@pytest.mark.parametrize("vec", [False, True], ids=["scalar", "vector"])
+def test_lb_fp32_close_to_fd(acs, vec):
+    phi0, eps, dt, h = _problem(3, 0, seed=5, vec=vec)
     p32 = phi0.astype(np.float32)
     a = acs.AllenCahn(phi0.shape, eps, dt, h, 0, "f32")
     a.use_lb_form()
