@@ -5,14 +5,14 @@
 // ld_i = n_i rounded up to a 16-byte multiple apart (acs_batch_row_strides), so
 // every instance has its own TMA tensor maps, one per ping-pong buffer.
 //
-// Work: every instance is cut into blocks of TX columns x 16 rows (TX = 128 FP32,
-// 64 FP64), listed instance after instance, down each column strip.  Each CTA owns
-// a contiguous run of that list and streams it through one ring of TMA-loaded boxes
-// exactly as the single-problem 2D kernel streams its column (same halo boxes, same
-// ghost rules, same per-point arithmetic and coefficients), so each instance is
-// bit-identical to its standalone run.  The ring runs on across block and instance
-// boundaries; at the end of its run a CTA meets the others at a software grid
-// barrier before the next step's loads are issued.
+// Work: every instance is cut into blocks of TX columns x TY rows (FP32 128 x 32,
+// FP64 64 x 16), listed instance after instance, down each column strip.  Per step,
+// CTAs draw blocks from a ticket counter and stream them through one ring of
+// TMA-loaded boxes, each block as the single-problem 2D kernel computes it (same halo
+// boxes, same ghost rules, same per-point arithmetic and coefficients), so each
+// instance is bit-identical to its standalone run.  The ring runs on across block and
+// instance boundaries; when the tickets run out a CTA meets the others at a software
+// grid barrier before the next step's loads are issued.
 //
 // The barrier spins with a one-second bound (%globaltimer); a CTA that gives up
 // records ACS_E_TIMEOUT and raises an abort flag that releases every other waiter,
@@ -47,12 +47,16 @@ struct BlockRef {
     int inst, x0, y0, colx, rowy, pad0, pad1, pad2;
 };
 
-// Tile geometry of the batched kernel: 2 rows per thread, 4 ring slots; blocks are
-// handed out in chunks of kChunk consecutive blocks (one tensor-map set per instance:
-// main box, column box, row box, for each of the two state buffers).
+// Tile geometry of the batched kernel.  FP32: 4 rows per thread (128 x 32 blocks), 3
+// ring slots, 3 CTAs per SM; FP64: 2 rows (64 x 16 blocks), 4 slots, 2 CTAs per SM
+// (4 rows spill there).  Blocks are handed out one at a time (kChunk consecutive
+// blocks per ticket).  Each instance has one tensor-map set: main box, column box,
+// row box, for each of the two state buffers.  Measured on the 256-instance workload
+// (FP32, GLUPS): 2 rows / 4 slots / chunks of 4: 592; 4 rows / 3 slots / chunks of 2:
+// 651; chunks of 1: 673; 4 rows / 4 slots: 615; 3 rows: 644.
 template <typename T>
-using BatchTile = Tile3<T, 2, 4>;
-constexpr int kChunk = 4;
+using BatchTile = Tile3<T, sizeof(T) == 4 ? 4 : 2, sizeof(T) == 4 ? 3 : 4>;
+constexpr int kChunk = 1;
 constexpr int kMapsPerInst = 6;
 constexpr int kFenceWords = 64;  // instances whose maps a CTA remembers as acquired
 
@@ -236,7 +240,7 @@ __device__ __forceinline__ void batch_block_any(const T* cur, const T* colb, con
 // warp) that every warp is done with it, so no compute warp waits for another and
 // only the producer waits, before it refills a slot.
 template <typename T>
-__global__ void __launch_bounds__(288, sizeof(T) == 4 ? 4 : 3) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
+__global__ void __launch_bounds__(288, sizeof(T) == 4 ? 3 : 2) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
                                                  const CUtensorMap* __restrict__ maps, int count,
                                                  const BlockRef* __restrict__ blocks, int nblocks, int nsteps,
                                                  BarrierState* bs, int* err) {
