@@ -2,10 +2,37 @@
 #pragma once
 
 #include <algorithm>
+#include <utility>
 
 #include "acs_device.cuh"
 
 namespace acs {
+
+// Programmatic dependent launch.  A kernel launched by launch_pdl() may be scheduled
+// while the kernel before it in the stream is still draining, which hides the launch
+// gap of a chain of short dependent kernels (small grids, one step per launch).  Every
+// such kernel calls pdl_wait() before it reads anything its predecessor wrote: the
+// wait returns once that predecessor has completed and its memory is visible (at once
+// when there is none).  pdl_trigger(), called by each CTA after its last store, lets
+// the successor be scheduled as this kernel's CTAs retire.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Reduction partial of one block: compensated FP64 sums of the bulk term
 // sum (phi^2 - 1)^2 / 4 and of the squared link differences, and max |phi|.

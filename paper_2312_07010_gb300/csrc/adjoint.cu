@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ C
                                                        const T* __restrict__ phin, const T* __restrict__ phin1,
                                                        const T* __restrict__ adj1, T* __restrict__ adj0, Geo g,
                                                        Coef<T> cf, int ybchunk, int* err, CSum* part) {
+    pdl_wait();  // the previous launch's stores (states, adjoint, partials) are visible from here on
     using TT = Tile3<T, 2, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, S = TT::S;
     constexpr int BOX = TT::SLOT_STRIDE / sizeof(T);  // elements per box (128-byte aligned)
@@ -402,6 +403,7 @@ __global__ void __launch_bounds__(256) k_adjoint2d_tma(const __grid_constant__ C
     const CSum t = cta_sum(tile_sum);
     const int cta = blockIdx.y * gridDim.x + blockIdx.x;
     if (tid == 0) part[cta] = cmerge(part[cta], t);
+    pdl_trigger();
 }
 
 // One adjoint step adding its per-block eps^2 partials into `part` (kMaxRedBlocks
@@ -435,10 +437,10 @@ static cudaError_t launch_adjoint(int dims, int bc, const T* phin, const T* phin
                                               : (bc == 1 ? k_adjoint2d_tma<T, 1, 2> : k_adjoint2d_tma<T, 2, 2>));
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
-                kern<<<dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), smem, st>>>(
-                    mp, mq, ml, phin, phin1, adj1, adj0, g, cf, ybchunk, err, part);
+                e = launch_pdl(kern, dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), smem, st, mp, mq, ml, phin,
+                               phin1, adj1, adj0, g, cf, ybchunk, err, part);
                 *nparts = ntx * nchunks;
-                return cudaGetLastError();
+                return e;
             }
         }
     }

@@ -38,6 +38,7 @@ __device__ __forceinline__ void axis_links_d(double& acc, double p, double up, i
 
 template <typename T, int D, int BC>
 __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g, RedPartial* part) {
+    pdl_wait();
     CSum bulk{0.0, 0.0}, link{0.0, 0.0};
     float mx = 0.0f;
     double mxd = 0.0;
@@ -97,10 +98,12 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g
     const CSum L = block_csum(link);
     const double M = block_max_nonneg(mxd);
     if (threadIdx.x == 0) part[blockIdx.x] = RedPartial{B.s, B.c, L.s, L.c, M, 0.0, 0.0, 0.0};
+    pdl_trigger();
 }
 
 __global__ void k_reduce_finish(const RedPartial* part, int nparts, double hd, double link_scale,
                                 double* out2) {
+    pdl_wait();
     FixAcc b, l;
     double m = 0.0;
 #pragma unroll 4
@@ -121,6 +124,7 @@ __global__ void k_reduce_finish(const RedPartial* part, int nparts, double hd, d
         out2[0] = hd * (0.25 * bulk + link_scale * links);
         out2[1] = M;
     }
+    pdl_trigger();
 }
 
 int reduce_blocks(const Geo& g) {
@@ -132,18 +136,18 @@ template <typename T>
 cudaError_t launch_reduce(int dims, int bc, const T* src, const Geo& g, double eps2, double h,
                           RedPartial* partials, double* out2, cudaStream_t st) {
     const int nb = reduce_blocks(g);
+    cudaError_t e = cudaSuccess;
 #define ACS_RED_CASE(D, B) \
-    if (dims == D && bc == B) k_reduce<T, D, B><<<nb, 256, 0, st>>>(src, g, partials); else
+    if (dims == D && bc == B) e = launch_pdl(k_reduce<T, D, B>, dim3(nb), dim3(256), 0, st, src, g, partials); else
     ACS_RED_CASE(1, 0) ACS_RED_CASE(1, 1) ACS_RED_CASE(1, 2)
     ACS_RED_CASE(2, 0) ACS_RED_CASE(2, 1) ACS_RED_CASE(2, 2)
     ACS_RED_CASE(3, 0) ACS_RED_CASE(3, 1) ACS_RED_CASE(3, 2)
     return cudaErrorInvalidValue;
 #undef ACS_RED_CASE
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const double hd = std::pow(h, (double)dims);
-    k_reduce_finish<<<1, 256, 0, st>>>(partials, nb, hd, 0.5 * eps2 / (h * h), out2);
-    return cudaGetLastError();
+    return launch_pdl(k_reduce_finish, dim3(1), dim3(256), 0, st, (const RedPartial*)partials, nb, hd,
+                      0.5 * eps2 / (h * h), out2);
 }
 
 template cudaError_t launch_reduce<float>(int, int, const float*, const Geo&, double, double, RedPartial*, double*, cudaStream_t);
@@ -151,8 +155,8 @@ template cudaError_t launch_reduce<double>(int, int, const double*, const Geo&, 
 
 cudaError_t launch_reduce_finish(const RedPartial* part, int nparts, int dims, double eps2, double h, double* out2,
                                  cudaStream_t st) {
-    k_reduce_finish<<<1, 256, 0, st>>>(part, nparts, std::pow(h, (double)dims), 0.5 * eps2 / (h * h), out2);
-    return cudaGetLastError();
+    return launch_pdl(k_reduce_finish, dim3(1), dim3(256), 0, st, part, nparts, std::pow(h, (double)dims),
+                      0.5 * eps2 / (h * h), out2);
 }
 
 // ---------------------------------------------------------------- phase volume

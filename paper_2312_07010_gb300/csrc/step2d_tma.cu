@@ -20,6 +20,7 @@ template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2)
     k_step2d_tma(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src, T* __restrict__ dst, Geo g,
                  Coef<T> c, int ybchunk, int* err, RedPartial* part) {
+    pdl_wait();  // the previous step's stores are visible from here on
     using TT = Tile3<T, RPT, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2)
         }
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 bool step2d_tma_supported(int dtype, const Geo& g) {
@@ -219,11 +221,10 @@ static cudaError_t launch2d_variant(int bc, const T* src, T* dst, const Geo& g, 
                             : (bc == 1 ? k_step2d_tma<T, 1, SV, RPT, SS, MODE> : k_step2d_tma<T, 2, SV, RPT, SS, MODE>);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM);
         if (e == cudaSuccess)
-            kern<<<dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), TT::SMEM, st>>>(map, src, dst, g, c, ybchunk,
-                                                                                        err, part);
+            e = launch_pdl(kern, dim3((unsigned)ntx, (unsigned)nchunks), dim3(32, 8), TT::SMEM, st, map, src, dst, g,
+                           c, ybchunk, err, part);
     });
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T>

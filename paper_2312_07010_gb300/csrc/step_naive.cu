@@ -29,6 +29,7 @@ __device__ __forceinline__ T nb_hi(const T* __restrict__ p, int64_t i, int64_t c
 template <typename T, int D, int BC, int SOLVE>
 __global__ void __launch_bounds__(256) k_step_naive(const T* __restrict__ src, T* __restrict__ dst,
                                                     Geo g, Coef<T> c) {
+    pdl_wait();
     for (int64_t z = blockIdx.z; z < g.nz; z += gridDim.z) {
         for (int64_t y = blockIdx.y; y < g.ny; y += gridDim.y) {
             const int64_t row = z * g.sz + y * g.sy;
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(256) k_step_naive(const T* __restrict__ src, T
             }
         }
     }
+    pdl_trigger();
 }
 
 static dim3 naive_grid(const Geo& g) {
@@ -67,8 +69,9 @@ cudaError_t launch_step_naive(int dims, int bc, const T* src, T* dst, const Geo&
     dim3 grid = naive_grid(g), block(256);
 #define ACS_NAIVE_CASE(D, B)                                                                 \
     if (dims == D && bc == B) {                                                              \
-        ACS_SOLVE_DISPATCH(c.solve, S, (k_step_naive<T, D, B, S><<<grid, block, 0, st>>>(src, dst, g, c))); \
-        return cudaGetLastError();                                                           \
+        cudaError_t e = cudaSuccess;                                                         \
+        ACS_SOLVE_DISPATCH(c.solve, S, (e = launch_pdl(k_step_naive<T, D, B, S>, grid, block, 0, st, src, dst, g, c))); \
+        return e;                                                                            \
     }
     ACS_NAIVE_CASE(1, 0) ACS_NAIVE_CASE(1, 1) ACS_NAIVE_CASE(1, 2)
     ACS_NAIVE_CASE(2, 0) ACS_NAIVE_CASE(2, 1) ACS_NAIVE_CASE(2, 2)
