@@ -26,6 +26,7 @@ template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_step3d(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src,
                                                 T* __restrict__ dst, Geo g, Coef<T> c, int ntx, int zchunk,
                                                 int* err, RedPartial* part) {
+    pdl_wait();  // the previous step's stores are visible from here on
     using TT = Tile3<T, RPT, SS>;
     constexpr int VX = TT::VX, TX = TT::TX, TY = TT::TY, BW = TT::BW, S = TT::S;
     constexpr int SLOT_ELEMS = TT::SLOT_STRIDE / sizeof(T);
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_s
         }
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 bool step3d_supported(int dtype, const Geo& g) {
@@ -285,11 +287,10 @@ static cudaError_t launch3d_variant(int bc, const T* src, T* dst, const Geo& g, 
             e = cudaErrorNotSupported;
         if (nparts) *nparts = ntx * nty * nzc;
         if (e == cudaSuccess)
-            kern<<<dim3((unsigned)(ntx * nty), (unsigned)nzc), dim3(32, 8), TT::SMEM, st>>>(map, src, dst, g, c, ntx,
-                                                                                              zchunk, err, part);
+            e = launch_pdl(kern, dim3((unsigned)(ntx * nty), (unsigned)nzc), dim3(32, 8), TT::SMEM, st, map, src, dst,
+                           g, c, ntx, zchunk, err, part);
     });
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T>
