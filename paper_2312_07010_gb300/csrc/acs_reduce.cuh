@@ -240,6 +240,61 @@ __device__ __forceinline__ double max_bits(double a, double b) {
     return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
 }
 
+// The energy reduction's block step in one pass: the exact sums of two FixAcc (bulk
+// and link terms) and the maximum of non-negative doubles, valid in thread 0.  One
+// barrier publishes every warp's exponent maxima, which each thread then folds itself,
+// and one more publishes the warp sums, so the block pays three barriers instead of
+// the fourteen of three separate reductions.
+struct Combined2 {
+    CSum b, l;
+    double m;
+};
+__device__ __forceinline__ Combined2 block_combine2(const FixAcc& b, const FixAcc& l, double m) {
+    struct W1 {
+        int bad, eb, el;
+    };
+    struct W2 {
+        Fix fb, fl;
+        long long m;
+    };
+    __shared__ W1 s1[32];
+    __shared__ W2 s2[32];
+    const int tid = block_tid(), lane = tid & 31, warp = tid >> 5, nw = block_nwarps();
+    W1 w{(int)__reduce_or_sync(0xffffffffu, (unsigned)(b.bad | (l.bad << 3))),
+         __reduce_max_sync(0xffffffffu, b.E), __reduce_max_sync(0xffffffffu, l.E)};
+    if (lane == 0) s1[warp] = w;
+    __syncthreads();
+    W1 t{0, 0, 0};
+    for (int k = 0; k < nw; ++k) {
+        const W1 v = s1[k];
+        t.bad |= v.bad;
+        t.eb = max(t.eb, v.eb);
+        t.el = max(t.el, v.el);
+    }
+    Fix fb = fix_shr(b.f, t.eb - b.E), fl = fix_shr(l.f, t.el - l.E);
+    long long mb = __double_as_longlong(m);
+    for (int off = 16; off > 0; off >>= 1) {
+        fb = fix_add(fb, fix_shfl_down(fb, off));
+        fl = fix_add(fl, fix_shfl_down(fl, off));
+        mb = max(mb, __shfl_down_sync(0xffffffffu, mb, off));
+    }
+    if (lane == 0) s2[warp] = W2{fb, fl, mb};
+    __syncthreads();
+    Combined2 r{CSum{0.0, 0.0}, CSum{0.0, 0.0}, 0.0};
+    if (tid == 0) {
+        for (int k = 1; k < nw; ++k) {
+            fb = fix_add(fb, s2[k].fb);
+            fl = fix_add(fl, s2[k].fl);
+            mb = max(mb, s2[k].m);
+        }
+        r.b = (t.bad & 7) ? nonfinite_sum(t.bad & 7) : fix_to_csum(fb, t.eb);
+        r.l = (t.bad >> 3) ? nonfinite_sum(t.bad >> 3) : fix_to_csum(fl, t.el);
+        r.m = __longlong_as_double(mb);
+    }
+    __syncthreads();  // s1 / s2 may be reused by a following call
+    return r;
+}
+
 // Block-wide maximum of non-negative doubles (NaN wins: as integers the bit patterns
 // of non-negative values, +Inf and positive NaN are ordered); valid in thread 0.
 __device__ __forceinline__ double block_max_nonneg(double v) {

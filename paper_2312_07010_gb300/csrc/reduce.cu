@@ -94,10 +94,13 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ src, Geo g
         cadd(link, dl);
     }
     // the bulk terms above are (p^2 - 1)^2; the 1/4 is applied at the end (exact)
-    const CSum B = block_csum(bulk);
-    const CSum L = block_csum(link);
-    const double M = block_max_nonneg(mxd);
-    if (threadIdx.x == 0) part[blockIdx.x] = RedPartial{B.s, B.c, L.s, L.c, M, 0.0, 0.0, 0.0};
+    FixAcc ab, al;
+    ab.add(bulk.s);
+    ab.add(bulk.c);
+    al.add(link.s);
+    al.add(link.c);
+    const Combined2 r = block_combine2(ab, al, mxd);
+    if (threadIdx.x == 0) part[blockIdx.x] = RedPartial{r.b.s, r.b.c, r.l.s, r.l.c, r.m, 0.0, 0.0, 0.0};
     pdl_trigger();
 }
 
@@ -115,14 +118,12 @@ __global__ void k_reduce_finish(const RedPartial* part, int nparts, double hd, d
         l.add(p.link_c);
         m = max_bits(m, p.mx);
     }
-    const CSum B = block_fixacc(b);
-    const CSum L = block_fixacc(l);
-    const double M = block_max_nonneg(m);
+    const Combined2 r = block_combine2(b, l, m);
     if (threadIdx.x == 0) {
-        const double bulk = B.s + B.c;
-        const double links = L.s + L.c;
+        const double bulk = r.b.s + r.b.c;
+        const double links = r.l.s + r.l.c;
         out2[0] = hd * (0.25 * bulk + link_scale * links);
-        out2[1] = M;
+        out2[1] = r.m;
     }
     pdl_trigger();
 }
