@@ -159,7 +159,10 @@ ACS_API int acs_get_kernel(const acs_ctx* ctx, int* kernel, int* depth);
  * Remark 1 for the summed value.  It is the form Eq. (IE-FD) removes; it is kept
  * to measure what the macroscopic form saves in memory and traffic.
  *
- * acs_lb_bytes  size of the population buffer: (2 dims + 1) * prod(n) elements.
+ * acs_lb_bytes  size of the population buffer: (2 dims + 1) * (prod(n) + 8192) elements;
+ *               population array k (k = 0; +x, +y, +z; -x, -y, -z) starts at element
+ *               k * (prod(n) + 8192) (the gap keeps the arrays off a common alignment in
+ *               the memory channels).
  * acs_lb_bind   d_pop: that many bytes, 16-byte aligned, caller-owned, valid while
  *               ACS_KERNEL_LB is selected; omega1: the weight w_1 in (0, 1/(2d)],
  *               or 0 for the paper's choice (1/3, 1/5, 1/6 for d = 1, 2, 3).

@@ -624,7 +624,7 @@ ACS_API int acs_get_kernel(const acs_ctx* c, int* kernel, int* depth) {
 }
 
 ACS_API size_t acs_lb_bytes(const acs_ctx* c) {
-    return c ? (size_t)(2 * c->dims + 1) * state_bytes(c) : 0;
+    return c ? (size_t)(2 * c->dims + 1) * (state_bytes(c) + (size_t)kLbGap * c->esize) : 0;
 }
 
 ACS_API int acs_lb_bind(acs_ctx* c, void* d_pop, size_t bytes, double omega1) {

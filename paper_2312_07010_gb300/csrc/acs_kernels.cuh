@@ -58,8 +58,12 @@ cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* d
                                  const Coef<T>& c, int* err, cudaStream_t st);
 bool tiled_supported(int dims, int dtype, const Geo& g);
 
-// Collide-and-stream (population) form of the step: pop holds (2 dims + 1) * total
-// values; omega1 is the lattice weight w_1 and lam = eps^2 dt / h^2 (s = w_1 / lam).
+// Collide-and-stream (population) form of the step: pop holds 2 dims + 1 arrays of
+// total values, kLbGap values apart; omega1 is the lattice weight w_1 and
+// lam = eps^2 dt / h^2 (s = w_1 / lam).  The gap keeps the arrays, whose size is
+// often a power of two, from starting on a common alignment: with all seven on one
+// alignment the gathering kernel ran 9 % slower at 512^3.
+constexpr int64_t kLbGap = 8192;
 template <typename T>
 cudaError_t launch_step_lb(int dims, int bc, const T* src, T* pop, T* dst, const Geo& g, double omega1,
                            double lam, const Coef<T>& cf, cudaStream_t st);

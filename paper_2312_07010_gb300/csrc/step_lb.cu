@@ -17,7 +17,7 @@
 // boundary node's own value (periodic: the wrapped node's stored population).
 //
 // The populations live in a caller buffer, one array of n^d values per direction
-// (k = 0; +x, +y, +z; -x, -y, -z).  Summed, the form equals Eq. (IE-FD) up to
+// (k = 0; +x, +y, +z; -x, -y, -z), n^d + kLbGap values apart.  Summed, the form equals Eq. (IE-FD) up to
 // rounding; it moves (2d+1) values out and back in per node where Eq. (IE-FD) moves
 // none, which is the memory and traffic cost the macroscopic form removes.
 #include "acs_kernels.cuh"
@@ -46,7 +46,7 @@ __device__ __forceinline__ T lb_nbr(const T* src, int64_t i, int64_t c, int64_t 
 template <typename T, int D, int BC>
 __global__ void __launch_bounds__(256) k_lb_collide(const T* __restrict__ src, T* __restrict__ pop, Geo g,
                                                     LbCoef<T> lc) {
-    const int64_t tot = g.total;
+    const int64_t tot = g.total + kLbGap;  // stride between population arrays
     for (int64_t z = blockIdx.z; z < g.nz; z += gridDim.z)
         for (int64_t y = blockIdx.y; y < g.ny; y += gridDim.y) {
             const int64_t row = z * g.sz + y * g.sy;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_lb_collide(const T* __restrict__ src, T
 template <typename T, int D, int BC, int SOLVE>
 __global__ void __launch_bounds__(256) k_lb_stream(const T* __restrict__ src, const T* __restrict__ pop,
                                                    T* __restrict__ dst, Geo g, LbCoef<T> lc, Coef<T> cf) {
-    const int64_t tot = g.total;
+    const int64_t tot = g.total + kLbGap;  // stride between population arrays
     for (int64_t z = blockIdx.z; z < g.nz; z += gridDim.z)
         for (int64_t y = blockIdx.y; y < g.ny; y += gridDim.y) {
             const int64_t row = z * g.sz + y * g.sy;
@@ -122,7 +122,7 @@ template <typename T, int D, int BC>
 __global__ void __launch_bounds__(256) k_lb_collide_v(const T* __restrict__ src, T* __restrict__ pop, Geo g,
                                                       LbCoef<T> lc) {
     constexpr int VX = 16 / sizeof(T);
-    const int64_t tot = g.total, nxv = g.nx / VX;
+    const int64_t tot = g.total + kLbGap, nxv = g.nx / VX;  // tot: array stride
     for (int64_t z = blockIdx.z; z < g.nz; z += gridDim.z)
         for (int64_t y = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; y < g.ny; y += (int64_t)gridDim.y * blockDim.y) {
             const int64_t row = z * g.sz + y * g.sy;
@@ -170,7 +170,7 @@ template <typename T, int D, int BC, int SOLVE>
 __global__ void __launch_bounds__(256) k_lb_stream_v(const T* __restrict__ src, const T* __restrict__ pop,
                                                      T* __restrict__ dst, Geo g, LbCoef<T> lc, Coef<T> cf) {
     constexpr int VX = 16 / sizeof(T);
-    const int64_t tot = g.total, nxv = g.nx / VX;
+    const int64_t tot = g.total + kLbGap, nxv = g.nx / VX;  // tot: array stride
     for (int64_t z = blockIdx.z; z < g.nz; z += gridDim.z)
         for (int64_t y = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; y < g.ny; y += (int64_t)gridDim.y * blockDim.y) {
             const int64_t row = z * g.sz + y * g.sy;

@@ -120,7 +120,7 @@ def test_unbound_context_rejects_device_calls(L):
 
 
 def test_lb_form_host_logic(L):
-    """Population form: buffer size (2d+1) n^d elements; weight and order checks.
+    """Population form: buffer size (2d+1) (n^d + 8192) elements; weight and order checks.
     The pointer is never dereferenced by these calls (no device work)."""
     fake = ctypes.c_void_p(1 << 20)
     for dims, n in ((1, (40,)), (2, (12, 10)), (3, (6, 5, 4))):
@@ -128,7 +128,7 @@ def test_lb_form_host_logic(L):
             rc, ctx = _create(L, dims, n, 0.02, 0.01, 0.1, 1, dtype)
             assert rc == 0
             tot = math.prod(n)
-            assert L.acs_lb_bytes(ctx) == (2 * dims + 1) * tot * es
+            assert L.acs_lb_bytes(ctx) == (2 * dims + 1) * (tot + 8192) * es
             # selecting the form before binding its buffer is out of order
             assert L.acs_set_kernel(ctx, 4, 1) == -6
             nb = L.acs_lb_bytes(ctx)
