@@ -641,10 +641,21 @@ def extras(P, args):
     ms_f = _time(fwd_only, 3)
     ms_p = _time(plain_fwd, 3)
     sp.close()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    # the same with every state stored (501 x 4 MiB): the backward sweep recomputes nothing
+    s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    s.set_state(phi0)
+    s.record_for_grad(w.steps, 1)
+    ms_fb1 = _time(fwd_bwd, 3)
     out["cfg5_adjoint_1024sq"] = {"fwd_bwd_ms_per_time_step": ms_fb / w.steps,
                                   "recording_fwd_ms_per_time_step": ms_f / w.steps,
                                   "plain_fwd_ms_per_time_step": ms_p / w.steps,
-                                  "fwd_bwd_over_plain_fwd": ms_fb / ms_p}
+                                  "fwd_bwd_over_plain_fwd": ms_fb / ms_p,
+                                  "checkpoint_every": 50,
+                                  "store_every_state_fwd_bwd_ms_per_time_step": ms_fb1 / w.steps,
+                                  "store_every_state_over_plain_fwd": ms_fb1 / ms_p}
     s.close()
     del s
     torch.cuda.empty_cache()

@@ -253,7 +253,9 @@ ACS_API int acs_run_logged(acs_ctx* ctx, int64_t n_steps, int64_t every, double*
  * acs_grad_work_bytes(ctx, max_steps, every) bytes; from then on acs_set_state
  * stores phi^0 and acs_step stores every `every`-th state.  acs_grad() then
  * recomputes each segment from its checkpoint and sweeps backwards over all steps
- * since acs_set_state, given d_dL_dphiT (the state's dtype), writing dL/dphi0 to
+ * since acs_set_state (with every = 1 each step writes straight into its checkpoint
+ * slot and nothing is recomputed: max_steps + 1 states of memory for about a quarter
+ * less work), given d_dL_dphiT (the state's dtype), writing dL/dphi0 to
  * d_dL_dphi0 (same dtype; may alias d_dL_dphiT) and dL/d(eps^2) (accumulated in
  * FP64) to *dL_deps2_host.  Synchronizes.  ACS_E_STATE if nothing was recorded,
  * ACS_E_NOMEM if more than max_steps steps were taken.

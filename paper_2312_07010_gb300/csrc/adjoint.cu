@@ -553,6 +553,18 @@ int grad_record_steps(acs_ctx* c, int64_t n) {
     const GradLayout L = layout(v, G.max_steps, G.every);
     const int64_t start = G.recorded;
     auto enqueue = [&](cudaStream_t st) -> bool {
+        if (G.every == 1) {
+            // every state is a checkpoint: each step writes straight into the next slot
+            // (no copies, and the backward sweep recomputes nothing); the context's
+            // state is then the last slot
+            for (int64_t j = 0; j < n; ++j) {
+                const char* src = G.buf + L.ckpt + L.sb * (size_t)(start + j);
+                char* dst = G.buf + L.ckpt + L.sb * (size_t)(start + j + 1);
+                if (ctx_launch_one(c, src, dst, st) != cudaSuccess) return false;
+            }
+            return cudaMemcpyAsync(v.phi, G.buf + L.ckpt + L.sb * (size_t)(start + n), (size_t)v.g.total * v.esize,
+                                   cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+        }
         int64_t rec = start, left = n;
         while (left > 0) {
             const int64_t k = std::min(left, G.every - (rec % G.every));
@@ -639,14 +651,16 @@ ACS_API int acs_grad(acs_ctx* c, const void* d_dL_dphiT, void* d_dL_dphi0, doubl
             const int64_t m = std::min(G.every, N - s0);
             char* ck = G.buf + L.ckpt + L.sb * (size_t)seg;
             const char* prev = ck;
-            for (int64_t j = 0; j < m; ++j) {
+            // with a checkpoint after every step the segment's end state is stored
+            const bool stored = G.every == 1;
+            for (int64_t j = 0; j < m && !stored; ++j) {
                 char* dst = G.buf + L.seg + L.sb * (size_t)j;
                 if (ctx_launch_one(c, prev, dst, s) != cudaSuccess) return false;
                 prev = dst;
             }
             for (int64_t k = m - 1; k >= 0; --k) {
                 const char* pk = k == 0 ? ck : G.buf + L.seg + L.sb * (size_t)(k - 1);
-                const char* pk1 = G.buf + L.seg + L.sb * (size_t)k;
+                const char* pk1 = stored ? ck + L.sb : G.buf + L.seg + L.sb * (size_t)k;
                 cudaError_t e;
                 CSum* row = part;
                 if (v.dtype == ACS_F32)

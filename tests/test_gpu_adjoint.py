@@ -178,3 +178,26 @@ def test_adjoint_full_size_fp64_dot_product(acs):
     se = 1e-7
     fde = (L(phi0, w.eps ** 2 + se) - L(phi0, w.eps ** 2 - se)) / (2 * se)
     assert ge == pytest.approx(fde, rel=1e-5)
+
+
+@pytest.mark.parametrize("shape,bc", [((40, 64), BCS[0]), ((33, 17, 12), BCS[1]), ((257,), BCS[2])], ids=str)
+def test_store_every_state_equals_checkpointed(acs, shape, bc):
+    """Checkpoints after every step (no recompute in the backward sweep) give the same
+    bits as checkpoints every 7 steps, and the state after the recording is the run's."""
+    h, eps, dt, phi0, target = _setup(shape, bc, 11 + bc)
+    steps = 23
+    out = []
+    for every in (1, 7):
+        s = acs.AllenCahn(shape, eps, dt, h, bc, "f64")
+        s.set_state(phi0)
+        s.record_for_grad(steps, every)
+        s.step(10)
+        s.step(13)
+        pT = s.numpy()
+        gT = 2 * (pT - target) / pT.size
+        g0, ge = s.grad(torch.from_numpy(gT).cuda())
+        out.append((pT, g0.cpu().numpy(), ge))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    assert np.abs(out[0][0] - oracle.run_fd(phi0, eps, dt, h, bc, steps)).max() <= 1e-12 * np.abs(out[0][0]).max()
