@@ -196,6 +196,8 @@ class AllenCahnFunction(torch.autograd.Function):
 
     forward(phi0, eps2, steps, dt, h, bc, checkpoint_every) runs the CUDA stepper
     with checkpoint recording; backward runs the hand-written adjoint (acs_grad).
+    checkpoint_every = 1 stores every state (steps + 1 of them) and the backward pass
+    recomputes nothing; larger values trade memory for one recomputed forward.
     """
 
     @staticmethod
