@@ -232,10 +232,10 @@ __device__ __forceinline__ void batch_block_any(const T* cur, const T* colb, con
 // Persistent cooperative kernel: nsteps steps of every instance.  Per step, CTAs take
 // chunks of kChunk consecutive blocks from the step's ticket counter (so instances of
 // different cost balance out), stream them through the TMA ring, and meet at the grid
-// barrier.  Thread 0 is the producer: it draws tickets one chunk ahead, issues each
-// block's loads into the next free slot with the block's description in `meta`, and
-// closes the step with an end marker (a slot whose mbarrier completes without data).
-// A ninth warp produces (its lane 0 only); the eight compute warps consume slots
+// barrier.  Lane 0 of a ninth warp is the producer: it draws tickets one chunk ahead,
+// issues each block's loads into the next free slot with the block's description in
+// `meta`, and closes the step with an end marker (a slot whose mbarrier completes
+// without data).  The eight compute warps consume slots
 // independently: `full[s]` says a slot has landed, `empty[s]` (one arrival per compute
 // warp) that every warp is done with it, so no compute warp waits for another and
 // only the producer waits, before it refills a slot.
