@@ -411,7 +411,11 @@ def main():
             P.ACS_KERNEL_TEMPORAL: f"temporal{K}_v{variant}"}[kernel]
     traffic = _traffic_from_profile(f"step3d_f32_neumann_512_{ktag}")
 
-    launches_per_step = (w.steps // K) + 2 * n_logs
+    # step launches, plus per logged state one reduction pass and its finishing launch;
+    # on the streamed 3D kernel every logged state but the last is reduced by the first
+    # step of its interval (fused), which leaves only the finishing launch
+    fused_logs = n_logs - 1 if kernel == P.ACS_KERNEL_TILED else 0
+    launches_per_step = (w.steps // K) + 2 * n_logs - fused_logs
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -304,10 +304,57 @@ static int maybe_autotune(acs_ctx* c);
 
 static cudaError_t enqueue_reduce(acs_ctx* c, const void* state, double* out2, cudaStream_t st);
 
+// `count` single steps from `src` (phi or other), alternating buffers, ending in phi.
+static cudaError_t enqueue_steps_from(acs_ctx* c, int64_t count, void* src, cudaStream_t st) {
+    void* a = src;
+    void* b = src == c->phi ? c->other : c->phi;
+    for (int64_t j = 0; j < count; ++j) {
+        cudaError_t e = launch_k(c, 1, a, b, st);
+        if (e != cudaSuccess) return e;
+        std::swap(a, b);
+    }
+    if (a != c->phi) return cudaMemcpyAsync(c->phi, a, state_bytes(c), cudaMemcpyDeviceToDevice, st);
+    return cudaSuccess;
+}
+
+// A logged 3D run on the streamed kernels: the first step of every logged interval also
+// reduces its input state (the fused mode of the 3D kernel), so those energies cost no
+// pass of their own; the last logged state is reduced on its own.  cudaErrorNotSupported
+// (before anything is enqueued) where the fused mode does not apply.
+static cudaError_t enqueue_run_fused(acs_ctx* c, int64_t n, int64_t every, cudaStream_t st) {
+    const bool rows16 = (c->g.nx * (int64_t)c->esize) % 16 == 0;
+    if (c->dims != 3 || c->kernel != ACS_KERNEL_TILED || !rows16 || !tiled_supported(c->dims, c->dtype, c->g) ||
+        every < 1)
+        return cudaErrorNotSupported;
+    const int64_t m = n / every + 1;
+    for (int64_t k = 0; k + 1 < m; ++k) {
+        int np = 0;
+        cudaError_t e =
+            c->dtype == ACS_F32
+                ? launch_step_energy3d<float>(c->bc, (const float*)c->phi, (float*)c->other, c->g, c->cf, c->err,
+                                              c->partials, &np, st)
+                : launch_step_energy3d<double>(c->bc, (const double*)c->phi, (double*)c->other, c->g, c->cd, c->err,
+                                               c->partials, &np, st);
+        if (e != cudaSuccess) return e;  // NotSupported can only come at k = 0 (same shape every time)
+        e = launch_reduce_finish(c->partials, np, c->dims, c->eps * c->eps, c->h, c->log + 2 * k, st);
+        if (e == cudaSuccess) e = enqueue_steps_from(c, every - 1, c->other, st);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = enqueue_reduce(c, c->phi, c->log + 2 * (m - 1), st);
+    const int64_t rest = n - (m - 1) * every;
+    if (e == cudaSuccess && rest > 0) e = enqueue_steps(c, rest, st);
+    return e;
+}
+
 // n steps with {E_h, max|phi|} of the states 0, every, 2 every, ... written to the
 // context's log (every = 0: the steps alone).
 static cudaError_t enqueue_run(acs_ctx* c, int64_t n, int64_t every, cudaStream_t st) {
     if (every <= 0) return enqueue_steps(c, n, st);
+    if (n >= every) {
+        const cudaError_t e = enqueue_run_fused(c, n, every, st);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+    }
     const int64_t m = n / every + 1;
     cudaError_t e = enqueue_reduce(c, c->phi, c->log, st);
     for (int64_t k = 1; k < m && e == cudaSuccess; ++k) {

@@ -74,6 +74,11 @@ bool temporal_supported(int dims, int dtype, int depth, const Geo& g);
 template <typename T>
 cudaError_t launch_energy3d(int bc, const T* src, const Geo& g, const Coef<T>& c, int* err, RedPartial* part,
                             int* nparts, cudaStream_t st);
+// One 3D step src -> dst with the E_h / max-norm partials of src into part (the
+// energy pass fused into the step; same conditions as launch_energy3d).
+template <typename T>
+cudaError_t launch_step_energy3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int* err,
+                                 RedPartial* part, int* nparts, cudaStream_t st);
 template <typename T>
 cudaError_t launch_energy2d(int bc, const T* src, const Geo& g, const Coef<T>& c, int* err, RedPartial* part,
                             int* nparts, cudaStream_t st);

@@ -22,6 +22,9 @@
 
 namespace acs {
 
+// A step that also reduces its input state (E_h, max-norm): both bodies in one pass.
+constexpr int kModeStepEnergy = 2;
+
 template <typename T, int BC, int SOLVE, int RPT, int SS, int MODE>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_step3d(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ src,
                                                 T* __restrict__ dst, Geo g, Coef<T> c, int ntx, int zchunk,
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_s
                     if (xlo) left = BC == ACS_BC_NEUMANN ? cz[rr][0] : src[rowoff + nx - 1];
                     if (xhi) right = BC == ACS_BC_NEUMANN ? cz[rr][VX - 1] : src[rowoff];
                 }
-                if (MODE == kModeEnergy) {
+                if (MODE != kModeStep) {
                     // E_h and max-norm of this (input) state: the forward link of every
                     // unknown along x, y, z (ghost-ruled neighbours as for the step), plus
                     // the links of the first unknowns to the zero Dirichlet boundary
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_s
                             }
                         }
                     }
-                    continue;
+                    if (MODE == kModeEnergy) continue;
                 }
 #pragma unroll
                 for (int v = 0; v < VX; ++v) {
@@ -183,9 +186,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_s
                     xi[rr * VX + v] = predictor(cz[rr][v], s, c);
                 }
             }
-            if (MODE == kModeEnergy) {
-                eacc.plane_done();
-            } else {
+            if (MODE != kModeStep) eacc.plane_done();
+            if (MODE != kModeEnergy) {
                 T out[NP];
                 roots<T, SOLVE, NP>(xi, out, c);
 #pragma unroll
@@ -218,10 +220,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2) k_s
     };
     // the reduction's long loop body is kept in one copy (the fix-ups test their own
     // rows), so the instruction cache holds it; the step runs a lean copy off the faces
-    if ((MODE == kModeEnergy && BC != ACS_BC_DIRICHLET) || edge) run(std::true_type());
+    if ((MODE != kModeStep && BC != ACS_BC_DIRICHLET) || edge) run(std::true_type());
     else run(std::false_type());
 
-    if (MODE == kModeEnergy) energy_block_write(eacc, part + (blockIdx.y * gridDim.x + blockIdx.x));
+    if (MODE != kModeStep) energy_block_write(eacc, part + (blockIdx.y * gridDim.x + blockIdx.x));
     if (failed) {
         // record the timeout, then let the newest load of every slot land (bounded)
         // before the CTA's shared memory goes away
@@ -283,7 +285,7 @@ static cudaError_t launch3d_variant(int bc, const T* src, T* dst, const Geo& g, 
         }
         const int nzc = (int)((g.nz + zchunk - 1) / zchunk);
         if (e == cudaSuccess && nzc > 65535) e = cudaErrorNotSupported;
-        if (e == cudaSuccess && MODE == kModeEnergy && (int64_t)ntx * nty * nzc > kMaxStreamParts)
+        if (e == cudaSuccess && MODE != kModeStep && (int64_t)ntx * nty * nzc > kMaxStreamParts)
             e = cudaErrorNotSupported;
         if (nparts) *nparts = ntx * nty * nzc;
         if (e == cudaSuccess)
@@ -310,6 +312,17 @@ cudaError_t launch_energy3d(int bc, const T* src, const Geo& g, const Coef<T>& c
                             int* nparts, cudaStream_t st) {
     return launch3d_variant<T, 2, 6, kModeEnergy>(bc, src, nullptr, g, c, 0, err, part, nparts, st);
 }
+// One step src -> dst that also forms the E_h / max-norm partials of src (the step's
+// own tiles and neighbours; the 4-slot tile shape whatever the context's variant).
+template <typename T>
+cudaError_t launch_step_energy3d(int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int* err,
+                                 RedPartial* part, int* nparts, cudaStream_t st) {
+    return launch3d_variant<T, 2, 4, kModeStepEnergy>(bc, src, dst, g, c, 0, err, part, nparts, st);
+}
+template cudaError_t launch_step_energy3d<float>(int, const float*, float*, const Geo&, const Coef<float>&, int*,
+                                                 RedPartial*, int*, cudaStream_t);
+template cudaError_t launch_step_energy3d<double>(int, const double*, double*, const Geo&, const Coef<double>&,
+                                                  int*, RedPartial*, int*, cudaStream_t);
 template cudaError_t launch_energy3d<float>(int, const float*, const Geo&, const Coef<float>&, int*, RedPartial*,
                                             int*, cudaStream_t);
 template cudaError_t launch_energy3d<double>(int, const double*, const Geo&, const Coef<double>&, int*, RedPartial*,

@@ -467,3 +467,36 @@ def test_mean_curvature_sphere_radius(acs):
     exact_drop = R0 - math.sqrt(R0 ** 2 - 4 * eps ** 2 * 40.0)
     assert drop == pytest.approx(exact_drop, rel=0.02)
     assert s.maxnorm() <= 1.0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape,steps,every", [((20, 37, 36), 30, 10), ((9, 16, 40), 25, 7), ((64, 64, 64), 10, 5)],
+                         ids=str)
+def test_logged_3d_run_fused_energy(acs, shape, bc, dtype, steps, every):
+    """A logged 3D run on the streamed kernel takes each interval's first energy from its
+    first step (fused mode): the states equal the one-thread kernel's bit for bit and every
+    logged E_h / max-norm matches the oracle's (E_h relative 1e-12)."""
+    h, eps, dt, phi0 = _problem(shape, bc, 70 + bc)
+    nd = np.float32 if dtype == "f32" else np.float64
+    p0 = phi0.astype(nd)
+    a = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    b = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    a.set_kernel(acs.ACS_KERNEL_TILED)
+    b.set_kernel(acs.ACS_KERNEL_NAIVE)
+    a.set_state(p0)
+    b.set_state(p0)
+    Ea, Ma = a.run_logged(steps, every)
+    Eb, Mb = b.run_logged(steps, every)
+    assert np.array_equal(a.numpy(), b.numpy())
+    np.testing.assert_array_equal(Ma, Mb)
+    # the oracle's energies of the GPU's own states (FP32 states are exact inputs)
+    c = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    c.set_kernel(acs.ACS_KERNEL_NAIVE)
+    c.set_state(p0)
+    ref = [oracle.energy(c.numpy().astype(np.float64), eps, dt, h, bc)]
+    for _ in range(steps // every):
+        c.step(every)
+        ref.append(oracle.energy(c.numpy().astype(np.float64), eps, dt, h, bc))
+    np.testing.assert_allclose(Ea, ref, rtol=1e-12)
+    np.testing.assert_allclose(Eb, ref, rtol=1e-12)
