@@ -1,5 +1,7 @@
-// acs_reduce.cuh -- compensated FP64 accumulation helpers shared by the
-// reduction kernels (energy / maximum norm, adjoint gradient sums).
+// acs_reduce.cuh -- accumulation helpers shared by the reduction kernels (energy /
+// maximum norm, phase volume, adjoint gradient sums): compensated FP64 sums within a
+// thread, exact float-pair terms for FP32 states, and the exact fixed-point
+// combination of partial sums across a block.
 #pragma once
 
 #include <climits>

@@ -10,8 +10,10 @@
 // has no cancellation, unlike the phi . (Lambda phi) form.
 //
 // Two stages, deterministic: a fixed grid (depending only on the shape) writes one
-// partial per block; one block combines them in a fixed order.  Each thread sums
-// with Neumaier's compensation; partials are combined with error-free TwoSum.
+// partial per block; one block combines them.  Each thread sums with Neumaier's
+// compensation (FP32 states: exact float-pair terms first); the threads' and the
+// blocks' sums are combined exactly in 128-bit fixed point (acs_reduce.cuh), so the
+// result does not depend on the order of the combination.
 #include "acs_kernels.cuh"
 #include "acs_reduce.cuh"
 
