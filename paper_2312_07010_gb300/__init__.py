@@ -6,7 +6,8 @@ package does not load the library; the first call that needs it does, and fails
 loudly when it has not been built (``paper_2312_07010_gb300.build.build()``).
 """
 from . import build
-from ._lib import (ACS_BC_DIRICHLET, ACS_BC_NEUMANN, ACS_BC_PERIODIC, ACS_F32, ACS_F64,
+from ._lib import (ACS_BC_DIRICHLET, ACS_BC_NEUMANN, ACS_BC_PERIODIC, ACS_E_CUDA, ACS_E_INVAL,
+                   ACS_E_NOMEM, ACS_E_NONFINITE, ACS_E_STATE, ACS_E_TIMEOUT, ACS_E_UNSUPPORTED, ACS_F32, ACS_F64,
                    ACS_KERNEL_AUTO, ACS_KERNEL_NAIVE, ACS_KERNEL_TEMPORAL, ACS_KERNEL_TILED,
                    ACS_SCHEME_FEX_FD, ACS_SCHEME_RLB_MIE_FD, SIGNATURES, AcsError, check, lib,
                    lib_path, strerror)
@@ -14,6 +15,8 @@ from ._lib import (ACS_BC_DIRICHLET, ACS_BC_NEUMANN, ACS_BC_PERIODIC, ACS_F32, A
 __all__ = [
     "build", "lib", "lib_path", "strerror", "check", "AcsError", "SIGNATURES",
     "ACS_BC_PERIODIC", "ACS_BC_NEUMANN", "ACS_BC_DIRICHLET", "ACS_F32", "ACS_F64",
+    "ACS_E_INVAL", "ACS_E_CUDA", "ACS_E_NOMEM", "ACS_E_TIMEOUT", "ACS_E_NONFINITE", "ACS_E_STATE",
+    "ACS_E_UNSUPPORTED",
     "ACS_KERNEL_AUTO", "ACS_KERNEL_NAIVE", "ACS_KERNEL_TILED", "ACS_KERNEL_TEMPORAL",
     "ACS_SCHEME_RLB_MIE_FD", "ACS_SCHEME_FEX_FD",
     "AllenCahn", "AllenCahnFunction", "allen_cahn", "Batch", "Lines", "Pipeline", "dt_max",

@@ -97,12 +97,15 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
     c.rb = (T)(1.0 / b);
     c.t = (T)(a / b);
     c.three_a = (T)(3.0 * a);
+    c.m2d = (T)(-2.0 * dims);
     if (scheme == ACS_SCHEME_FEX_FD) {
         c.a = (T)dt;
+        c.na = (T)(-dt);
         c.c0 = (T)(1.0 - 2.0 * dims * lam + dt);
         c.solve = kSolveFex;
     } else {
         c.a = (T)a;
+        c.na = (T)(-a);
         c.c0 = (T)(1.0 - 2.0 * dims * lam + a);
         const int nt = SeriesTerms<T>::value;
         const double t = a / b, rb = 1.0 / b;
@@ -123,6 +126,9 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
                 c.q[k] = (T)(kLagrangeC[k] * ak / std::pow(b, 3.0 * k + 1.0));
                 ak *= -a;
             }
+            // FP32 sums R = P - 1 and forms theta = xi + xi R: its constant term is
+            // 1/b - 1 = a/b, computed without cancellation
+            if (IncForm<T>::value) c.q[0] = (T)(a / b);
         } else {
             c.solve = kSolveNewton;
         }
@@ -251,7 +257,7 @@ static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaS
         if (c->kernel == ACS_KERNEL_LB)
             return launch_step_lb<float>(c->dims, c->bc, s, (float*)c->pop, d, c->g, c->omega1, c->lam, c->cf, st);
         if (c->kernel == ACS_KERNEL_TEMPORAL)
-            return launch_step_temporal<float>(c->dims, c->bc, k, s, d, c->g, c->cf, c->err, st);
+            return launch_step_temporal<float>(c->dims, c->bc, k, s, d, c->g, c->cf, c->variant, c->zchunk, c->err, st);
         if (c->kernel == ACS_KERNEL_TILED)
             return launch_step_tiled<float>(c->dims, c->bc, s, d, c->g, c->cf, c->variant, c->zchunk, c->err, st);
         return launch_step_naive<float>(c->dims, c->bc, s, d, c->g, c->cf, st);
@@ -261,7 +267,7 @@ static cudaError_t launch_k(acs_ctx* c, int k, const void* src, void* dst, cudaS
     if (c->kernel == ACS_KERNEL_LB)
         return launch_step_lb<double>(c->dims, c->bc, s, (double*)c->pop, d, c->g, c->omega1, c->lam, c->cd, st);
     if (c->kernel == ACS_KERNEL_TEMPORAL)
-        return launch_step_temporal<double>(c->dims, c->bc, k, s, d, c->g, c->cd, c->err, st);
+        return launch_step_temporal<double>(c->dims, c->bc, k, s, d, c->g, c->cd, c->variant, c->zchunk, c->err, st);
     if (c->kernel == ACS_KERNEL_TILED)
         return launch_step_tiled<double>(c->dims, c->bc, s, d, c->g, c->cd, c->variant, c->zchunk, c->err, st);
     return launch_step_naive<double>(c->dims, c->bc, s, d, c->g, c->cd, st);
@@ -546,12 +552,7 @@ ACS_API int acs_create(int dims, const int64_t n[3], double eps, double dt, doub
     if (!std::isfinite(eps) || !std::isfinite(dt) || !std::isfinite(h)) return ACS_E_INVAL;
     if (eps < 0 || !(h > 0) || !(dt > 0) || !(dt < 2)) return ACS_E_INVAL;
     if (bc < 0 || bc > 2 || (dtype != ACS_F32 && dtype != ACS_F64)) return ACS_E_INVAL;
-    int64_t total = 1;
-    for (int k = 0; k < dims; ++k) {
-        if (n[k] < 1 || n[k] > (int64_t(1) << 40)) return ACS_E_INVAL;
-        total *= n[k];
-        if (total > (int64_t(1) << 40)) return ACS_E_INVAL;
-    }
+    if (!shape_ok(dims, n)) return ACS_E_INVAL;
     acs_ctx* c = new (std::nothrow) acs_ctx();
     if (!c) return ACS_E_NOMEM;
     c->dims = dims;

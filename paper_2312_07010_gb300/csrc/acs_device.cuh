@@ -26,20 +26,35 @@ struct NewtonMax { static constexpr int value = sizeof(T) == 4 ? 4 : 6; };
 
 // Coefficients of one step in the state's precision T.
 //   lam = eps^2 dt / h^2 (Eq. IE-FD-vector-form), a = dt/2, b = 1 - a.
-//   xi = c0 phi - a phi^3 + lam S, S = sum of the 2d neighbours, c0 = 1 - 2 d lam + a
-// (Remark 1's xi = (1 - 2 d lam) phi - (dt/2)(phi^3 - phi) + lam S, regrouped).
-// For the FEX-FD scheme of Remark 2 the same expression with a = dt,
-// c0 = 1 - 2 d lam + dt is the new state and no cubic is solved.
+// Remark 1's explicit part xi = (1 - 2 d lam) phi - (dt/2)(phi^3 - phi) + lam S, with
+// S the sum of the 2d neighbours, is evaluated
+//   FP64:  xi = c0 phi - a phi^3 + lam S,           c0 = 1 - 2 d lam + a;
+//   FP32:  xi = phi + [lam (S - 2 d phi) + (-a) phi (phi^2 - 1)]   (increment form;
+//          each operation of it has a packed two-lane FP32 instruction, see f32x2.cuh).
+// The FP32 form keeps the rounded coefficients (lam, a) on the small increment only:
+// with c0 (and 1/b below) rounded to FP32, every step carries the same relative
+// error of up to 4e-8 in phi, which accumulates near a moving interface (2.7e-5
+// after 2000 steps of the 4096^2 Dirichlet star run against 5.8e-6 in this form).
+// For the FEX-FD scheme of Remark 2 the same expression with a = dt is the new
+// state and no cubic is solved.
 //
 // The root theta of a theta^3 + b theta = xi (Remark 1) as a series in xi
 // (Lagrange inversion): with x = xi/b, y = (a/b) x^2,
 //   theta = x sum_k (-y)^k C_k,  C_k = binom(3k, k) / (2k + 1)  (1, 1, 3, 12, 55, ...),
 // convergent for y < 4/27; so theta = xi sum_k q_k (xi^2)^k with
 //   q_k = C_k (-a)^k / b^(3k+1).
+// FP64 evaluates theta = xi P(xi^2) with P = sum_k q_k x2^k; FP32 evaluates
+// theta = xi + xi R(xi^2) with R = P - 1 (its constant term q_0 - 1 = a/b), for the
+// same reason as the increment form.
+template <typename T>
+struct IncForm { static constexpr bool value = sizeof(T) == 4; };
+
 template <typename T>
 struct Coef {
     T lam, c0, a, b, three_a;
-    T q[10];      // kSolveSeries: theta = xi * sum_k q[k] xi^(2k)
+    T m2d;        // -2 d (exact), the increment form's Laplacian weight of phi
+    T na;         // -a, the increment form's reaction weight
+    T q[10];      // kSolveSeries: theta = xi * sum_k q[k] xi^(2k) (FP32: q[0] = a/b, theta = xi + xi * sum)
     T xi2max;     // kSolveSeries applies while xi^2 <= xi2max
     T fast2max;   // several-points fast path (tiled kernels): xi^2 bound, see roots()
     T rb, t;      // kSolveNewton: 1/b, a/b
@@ -67,6 +82,15 @@ __device__ __forceinline__ float arcp(float x) {
 }
 __device__ __forceinline__ double arcp(double x) { return (double)arcp((float)x); }
 
+// p(theta) = a theta^3 + b theta - xi, given th2 = theta^2.  FP32 writes it as
+// (theta - xi) + a (theta^3 - theta), which does not use the rounded b (a bias in b
+// would move the root itself, not only the convergence).
+template <typename T>
+__device__ __forceinline__ T residual(T th, T th2, T xi, T a, T b) {
+    if (IncForm<T>::value) return dfma(a, dfma(th2, th, -th), th - xi);
+    return dfma(dfma(a, th2, b), th, -xi);
+}
+
 // Robust root of a theta^3 + b theta = xi for any xi (used when the fast path does
 // not apply, e.g. when the maximum-principle condition is violated).  p is odd and
 // increasing, so solve for |xi| and restore the sign.  Newton from
@@ -82,7 +106,7 @@ __device__ __noinline__ T cubic_robust(T xi, T a, T b) {
     if (cb < th) th = cb;
     for (int it = 0; it < 200; ++it) {
         T th2 = th * th;
-        T p = dfma(dfma(a, th2, b), th, -ax);
+        T p = residual(th, th2, ax, a, b);
         T nt = th - p / dfma(T(3) * a, th2, b);
         if (!(nt < th)) break;
         th = nt;
@@ -112,7 +136,7 @@ __device__ __forceinline__ T newton_fix(T th, T xi, const Coef<T>& c) {
     for (int k = 0; k < NewtonMax<T>::value; ++k) {
         if (k < c.newton) {
             const T th2 = th * th;
-            const T p = dfma(dfma(c.a, th2, c.b), th, -xi);
+            const T p = residual(th, th2, xi, c.a, c.b);
             const T dp = dfma(c.three_a, th2, c.b);
             th = dfma(-p, arcp(dp), th);
         }
@@ -120,21 +144,50 @@ __device__ __forceinline__ T newton_fix(T th, T xi, const Coef<T>& c) {
     return th;
 }
 
+// The truncated Lagrange series at xi (x2 = xi^2): xi P(x2), or xi + xi R(x2) in FP32.
+template <typename T, int NT>
+__device__ __forceinline__ T series_eval(T xi, T x2, const Coef<T>& c) {
+    T P = c.q[NT - 1];
+#pragma unroll
+    for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2, c.q[k]);
+    return IncForm<T>::value ? dfma(xi, P, xi) : xi * P;
+}
+
 // Root of theta + (dt/2) f(theta) = xi (Remark 1), i.e. a theta^3 + b theta = xi.
 // The host picks the mode and its limits from a-priori error bounds so that the
 // fast paths are accurate to the last bit of T for |xi| <= 1.001 (Theorem 2's
 // range plus rounding); larger |xi| take the robust path.
+// x limited to [-1, 1]; NaN passes through (PTX max.NaN / min.NaN).
+__device__ __forceinline__ float clamp_unit(float x) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(-1.0f));
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(r), "f"(1.0f));
+    return r;
+}
+
+// FP32 series solve while Theorem 2's condition holds (c.clamp): with |phi| <= 1 the
+// exact predictor obeys |xi| <= 1 (its explicit part is a convex combination), so xi
+// is limited to [-1, 1] (a no-op in exact arithmetic), and then |theta| <= 1 needs no
+// guard: the series' truncation error (<= 2^-26, chosen by the host for
+// |xi| <= 1.001) and the rounding of R stay below the 2^-24 gap above 1, so xi = +-1
+// gives +-1 exactly and |xi| < 1 gives |theta| <= 1.
+template <typename T>
+__device__ __forceinline__ T series_root_unit(T xi, const Coef<T>& c) {
+    const T xc = clamp_unit(xi);
+    return series_eval<T, SeriesTerms<T>::value>(xc, xc * xc, c);
+}
+
 template <typename T, int SOLVE>
 __device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
     T th;
+    if constexpr (IncForm<T>::value && SOLVE == kSolveSeries) {
+        if (c.clamp) return series_root_unit(xi, c);
+    }
     if (SOLVE == kSolveSeries) {
         constexpr int NT = SeriesTerms<T>::value;
         const T x2 = xi * xi;
         if (x2 <= c.xi2max) {
-            T P = c.q[NT - 1];
-#pragma unroll
-            for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2, c.q[k]);
-            th = xi * P;
+            th = series_eval<T, NT>(xi, x2, c);
         } else {
             th = cubic_robust(xi, c.a, c.b);
         }
@@ -164,6 +217,11 @@ __device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
 // the explicit predictor xi, the series root without its range check, the clamp.
 template <typename T>
 __device__ __forceinline__ T predictor(T p, T s, const Coef<T>& c) {
+    if (IncForm<T>::value) {
+        const T lap = dfma(c.m2d, p, s);       // S - 2 d phi
+        const T cub = p * dfma(p, p, T(-1));   // phi^3 - phi = phi (phi^2 - 1)
+        return p + dfma(c.lam, lap, c.na * cub);
+    }
     const T p2 = p * p;
     return dfma(c.lam, s, p * dfma(-c.a, p2, c.c0));
 }
@@ -171,8 +229,7 @@ __device__ __forceinline__ T predictor(T p, T s, const Coef<T>& c) {
 // ghost-ruled neighbours.
 template <typename T, int SOLVE>
 __device__ __forceinline__ T update(T p, T s, const Coef<T>& c) {
-    const T p2 = p * p;
-    const T xi = dfma(c.lam, s, p * dfma(-c.a, p2, c.c0));
+    const T xi = predictor(p, s, c);
     if (SOLVE == kSolveFex) return xi;
     return cubic_root<T, SOLVE>(xi, c);
 }

@@ -53,6 +53,19 @@ struct CtxView {
     GradState* grad;
 };
 
+// Shape limit of every entry point: 1 <= n[k] and prod(n) <= 2^40 elements.  Each
+// factor is checked against the limit divided by the product so far, before the
+// multiplication, so no int64 product can wrap around.
+constexpr int64_t kMaxElements = int64_t(1) << 40;
+inline bool shape_ok(int dims, const int64_t* n) {
+    int64_t total = 1;
+    for (int k = 0; k < dims; ++k) {
+        if (n[k] < 1 || n[k] > kMaxElements / total) return false;
+        total *= n[k];
+    }
+    return true;
+}
+
 template <typename T>
 Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok);
 Geo make_geo(int dims, const int64_t* n);

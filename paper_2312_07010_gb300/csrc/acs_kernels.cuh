@@ -53,9 +53,12 @@ cudaError_t launch_step_naive(int dims, int bc, const T* src, T* dst, const Geo&
 template <typename T>
 cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo& g, const Coef<T>& c, int variant,
                               int chunk, int* err, cudaStream_t st);
+// Temporal blocking: `depth` fused steps per pass (1 = the tiled kernel); chunk:
+// 16-row blocks per warp (2D), 0 = chosen from the occupancy.
+constexpr int kMaxTemporalDepth2d = 4;
 template <typename T>
 cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* dst, const Geo& g,
-                                 const Coef<T>& c, int* err, cudaStream_t st);
+                                 const Coef<T>& c, int variant, int chunk, int* err, cudaStream_t st);
 bool tiled_supported(int dims, int dtype, const Geo& g);
 
 // Collide-and-stream (population) form of the step: pop holds 2 dims + 1 arrays of

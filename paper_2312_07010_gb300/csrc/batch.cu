@@ -112,7 +112,8 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned nblocks,
         uint32_t i = 0;
         while (*vgen == g) {
             if (*vabort) { ok = 0; break; }
-            if ((++i & 63u) == 0u && global_ns() - t0 > kWaitNs) {
+            // about one second of %globaltimer, or kSpinLimit polls if the timer stalls
+            if (((++i & 63u) == 0u && global_ns() - t0 > kWaitNs) || i >= kSpinLimit) {
                 atomicExch(err, 1);
                 atomicExch(&bs->abort, 1);
                 ok = 0;

@@ -29,7 +29,9 @@ void* g_scratch[kMaxDevices] = {nullptr};
 
 // Device address of g_noalloc_partials on the current device, looked up once per
 // device.  In host code the array's name is only a host-side stand-in, so it is
-// never passed to a kernel directly.
+// never passed to a kernel directly.  The cached address belongs to the device's
+// primary context: a process that resets a device (cudaDeviceReset) must not call
+// acs_observe_noalloc on it again.
 cudaError_t scratch_for_current_device(RedPartial** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -58,14 +60,10 @@ extern "C" ACS_API int acs_observe_noalloc(int dims, const int64_t n[3], double 
     if (bc < 0 || bc > 2 || (dtype != ACS_F32 && dtype != ACS_F64)) return ACS_E_INVAL;
     const size_t esize = dtype == ACS_F32 ? 4 : 8;
     if (((uintptr_t)d_phi % esize) || ((uintptr_t)d_out2 % 8)) return ACS_E_INVAL;
-    int64_t nn[3] = {1, 1, 1}, total = 1;
-    for (int k = 0; k < dims; ++k) {
-        // the same shape limit as acs_create: at most 2^40 elements
-        if (n[k] < 1 || n[k] > (int64_t(1) << 40)) return ACS_E_INVAL;
-        total *= n[k];
-        if (total > (int64_t(1) << 40)) return ACS_E_INVAL;
-        nn[k] = n[k];
-    }
+    // the same shape limit as acs_create: at most 2^40 elements
+    if (!shape_ok(dims, n)) return ACS_E_INVAL;
+    int64_t nn[3] = {1, 1, 1};
+    for (int k = 0; k < dims; ++k) nn[k] = n[k];
     const Geo g = make_geo(dims, nn);
     if (reduce_blocks(g) > kNoAllocParts) return ACS_E_INVAL;  // would not fit the static scratch
     RedPartial* parts = nullptr;

@@ -58,8 +58,14 @@ bool tiled_supported(int dims, int dtype, const Geo& g) {
     return false;
 }
 
+bool step2d_tb_supported(int dtype, int depth, const Geo& g);
+template <typename T>
+cudaError_t launch_step2d_tb(int bc, int depth, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ych,
+                             cudaStream_t st);
+
+// Temporal blocking: 2D grids whose rows are a multiple of 16 bytes, depth 2..4.
 bool temporal_supported(int dims, int dtype, int depth, const Geo& g) {
-    (void)dims; (void)dtype; (void)depth; (void)g;
+    if (dims == 2) return step2d_tb_supported(dtype, depth, g);
     return false;
 }
 
@@ -74,8 +80,14 @@ cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo&
     }
     return cudaErrorNotSupported;
 }
+// `depth` fused steps src -> dst; a depth of 1 (the remainder of a run) is the
+// single-step tiled kernel, which rounds identically.  chunk: 16-row blocks per warp
+// (0 = chosen from the occupancy).
 template <typename T>
-cudaError_t launch_step_temporal(int, int, int, const T*, T*, const Geo&, const Coef<T>&, int*, cudaStream_t) {
+cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* dst, const Geo& g, const Coef<T>& c,
+                                 int variant, int chunk, int* err, cudaStream_t st) {
+    if (depth == 1) return launch_step_tiled<T>(dims, bc, src, dst, g, c, variant, 0, err, st);
+    if (dims == 2) return launch_step2d_tb<T>(bc, depth, src, dst, g, c, 16 * chunk, st);
     return cudaErrorNotSupported;
 }
 template cudaError_t launch_step_tiled<float>(int, int, const float*, float*, const Geo&, const Coef<float>&, int,
@@ -83,9 +95,9 @@ template cudaError_t launch_step_tiled<float>(int, int, const float*, float*, co
 template cudaError_t launch_step_tiled<double>(int, int, const double*, double*, const Geo&, const Coef<double>&,
                                                int, int, int*, cudaStream_t);
 template cudaError_t launch_step_temporal<float>(int, int, int, const float*, float*, const Geo&,
-                                                 const Coef<float>&, int*, cudaStream_t);
+                                                 const Coef<float>&, int, int, int*, cudaStream_t);
 template cudaError_t launch_step_temporal<double>(int, int, int, const double*, double*, const Geo&,
-                                                  const Coef<double>&, int*, cudaStream_t);
+                                                  const Coef<double>&, int, int, int*, cudaStream_t);
 
 // Static choice for problems the autotuner does not time (below 2^20 unknowns).  The
 // tiled kernels give a CTA a whole tile (16 rows of 64 FP64 / 128 FP32 values, times

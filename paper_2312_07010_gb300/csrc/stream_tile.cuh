@@ -134,9 +134,10 @@ constexpr int kNumTileVariants = 3;
         }                                                     \
     } while (0)
 
-// Cubic root of the RPT x VX values of one thread.  With the series solve and every
-// xi^2 <= fast2max, the series is evaluated without per-point checks and (when the
-// rounding guard is on) clamped with plain min/max: fast2max keeps |xi| <= 1 + 8 ulp,
+// Cubic root of the RPT x VX values of one thread.  FP32 with the series solve and
+// Theorem 2's condition: series_root_unit() per point.  Otherwise, with the series
+// solve and every xi^2 <= fast2max, the series is evaluated without per-point checks
+// and (when the rounding guard is on) clamped with plain min/max: fast2max keeps |xi| <= 1 + 8 ulp,
 // where the exact root is within [-1, 1] to rounding, so this gives the same values
 // as the per-point path.  The Newton solve does the same once every point is within
 // its seed's range.  Otherwise every point takes cubic_root().
@@ -146,6 +147,13 @@ __device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<
 #pragma unroll
         for (int i = 0; i < N; ++i) out[i] = xi[i];
         return;
+    }
+    if constexpr (IncForm<T>::value && SOLVE == kSolveSeries) {
+        if (c.clamp) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) out[i] = series_root_unit(xi[i], c);
+            return;
+        }
     }
     if (SOLVE == kSolveSeries) {
         T x2[N];
@@ -159,10 +167,7 @@ __device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<
             constexpr int NT = SeriesTerms<T>::value;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                T P = c.q[NT - 1];
-#pragma unroll
-                for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2[i], c.q[k]);
-                T th = xi[i] * P;
+                T th = series_eval<T, NT>(xi[i], x2[i], c);
                 if (c.clamp) th = fmin(fmax(th, T(-1)), T(1));
                 out[i] = th;
             }
@@ -203,7 +208,7 @@ __device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<
 #pragma unroll
                     for (int i = 0; i < N; ++i) {
                         const T th2 = th[i] * th[i];
-                        const T p = dfma(dfma(c.a, th2, c.b), th[i], -xi[i]);
+                        const T p = residual(th[i], th2, xi[i], c.a, c.b);
                         const T dp = dfma(c.three_a, th2, c.b);
                         th[i] = dfma(-p, arcp(dp), th[i]);
                     }

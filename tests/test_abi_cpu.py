@@ -57,6 +57,8 @@ def test_create_validates_arguments(L):
         (1, (8,), -0.1, 0.01, 0.1, 0), (1, (8,), 0.02, 0.0, 0.1, 0), (1, (8,), 0.02, 2.0, 0.1, 0),
         (1, (8,), 0.02, 0.01, 0.0, 0), (1, (8,), 0.02, 0.01, 0.1, 3), (1, (8,), math.nan, 0.01, 0.1, 0),
         (1, (8,), 0.02, math.inf, 0.1, 0), (3, (1 << 14, 1 << 14, 1 << 14), 0.02, 0.01, 0.1, 0),
+        # (2^24 + 1) * 2^40 wraps to 2^40 in int64: rejected before the product is formed
+        (2, ((1 << 24) + 1, 1 << 40), 0.02, 0.01, 0.1, 0), (3, (3, 1 << 62, 1 << 62), 0.02, 0.01, 0.1, 0),
     ]
     for args in bad:
         rc, ctx = _create(L, *args)
@@ -64,6 +66,15 @@ def test_create_validates_arguments(L):
         assert not ctx.value
     rc, ctx = _create(L, 1, (8,), 0.02, 0.01, 0.1, 0, dtype=7)
     assert rc == -1
+
+
+def test_noalloc_rejects_overflowing_shapes_on_host(L):
+    """acs_observe_noalloc validates the shape before any CUDA call, with the same
+    overflow-safe limit as acs_create; the device pointers here are never touched."""
+    fake = ctypes.c_void_p(1 << 20)  # aligned, never dereferenced: the call returns first
+    for dims, n in ((2, ((1 << 24) + 1, 1 << 40)), (3, (1 << 21, 1 << 21, 1)), (2, (0, 8))):
+        arr = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+        assert L.acs_observe_noalloc(dims, arr, 0.1, 0.1, 0, 0, fake, fake, None) == -1
 
 
 def test_create_warns_on_step_conditions(L):

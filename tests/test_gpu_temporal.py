@@ -1,0 +1,132 @@
+"""GPU parity of the temporally blocked step (K fused steps per pass, ACS_KERNEL_TEMPORAL).
+
+A pass of depth K computes every intermediate level with the single-step arithmetic
+(Eq. IE-FD, Remark 1) and re-applies the ghost rule of Eq. (Ddeltax) at each level, so
+K steps through it equal K single steps bit for bit.  Checked against the one-thread
+kernel for K = 2, 3, 4, every boundary, both precisions, grids smaller than one strip,
+partial strips and partial row chunks, step counts that are not multiples of K, and
+against the FP64 oracle (max-abs relative 1e-12).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import BC_DIRICHLET, BC_NEUMANN, BC_PERIODIC, cfg3, dt_rule, uniform_field
+
+pytestmark = pytest.mark.gpu
+
+BCS = [BC_PERIODIC, BC_NEUMANN, BC_DIRICHLET]
+BCN = {0: "P", 1: "HN", 2: "HD"}
+
+
+@pytest.fixture(scope="module")
+def acs():
+    import paper_2312_07010_gb300 as P
+    P.build.build()
+    P.lib()
+    return P
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _pair(acs, shape, bc, dtype, seed, depth, chunk=0):
+    n = max(shape)
+    h, eps = 1.0 / n, 0.02
+    dt = dt_rule(len(shape), eps, h)
+    phi0 = uniform_field(shape, -1.0, 1.0, seed)
+    a = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    b = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    a.set_kernel(acs.ACS_KERNEL_TEMPORAL, depth)
+    if chunk:
+        acs.check(acs.lib().acs_set_variant(a.ctx, 0, chunk))
+    b.set_kernel(acs.ACS_KERNEL_NAIVE)
+    a.set_state(phi0)
+    b.set_state(phi0)
+    return a, b, phi0, (eps, dt, h)
+
+
+# rows a multiple of 16 bytes in both precisions: x sizes multiple of 4
+SHAPES = [(1, 4), (3, 8), (7, 4), (33, 64), (130, 256), (61, 124), (257, 260), (40, 512)]
+
+
+@pytest.mark.parametrize("depth", [2, 3, 4])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", SHAPES, ids=str)
+def test_temporal2d_bitwise_equals_single_steps(acs, shape, bc, dtype, depth):
+    a, b, phi0, (eps, dt, h) = _pair(acs, shape, bc, dtype, 300 + bc + depth, depth)
+    assert a.get_kernel() == (acs.ACS_KERNEL_TEMPORAL, depth)
+    a.step(13)   # passes of depth K plus a remainder
+    b.step(13)
+    assert np.array_equal(a.numpy(), b.numpy())
+    if dtype == "f64":
+        assert relerr(a.numpy(), oracle.run_fd(phi0, eps, dt, h, bc, 13)) <= 1e-12
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 5])
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+def test_temporal2d_row_chunks(acs, bc, chunk):
+    """Explicit row chunks (16, 32, 80 rows per warp) that leave a partial last chunk."""
+    a, b, _, _ = _pair(acs, (203, 376), bc, "f32", 400 + bc, 4, chunk)
+    a.step(24)
+    b.step(24)
+    assert np.array_equal(a.numpy(), b.numpy())
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_temporal2d_cfg3_full_grid(acs, dtype):
+    """The 4096^2 Dirichlet star grid, 40 steps at depth 4, equals the TMA-streamed
+    single-step kernel bit for bit."""
+    w = cfg3(dtype)
+    nd = np.float32 if dtype == "f32" else np.float64
+    phi0 = w.phi0().astype(nd)
+    a = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, dtype)
+    b = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, dtype)
+    a.set_kernel(acs.ACS_KERNEL_TEMPORAL, 4)
+    b.set_kernel(acs.ACS_KERNEL_TILED)
+    a.set_state(phi0)
+    b.set_state(phi0)
+    a.step(40)
+    b.step(40)
+    assert np.array_equal(a.numpy(), b.numpy())
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+def test_temporal2d_fex_scheme(acs, bc):
+    """The FEX-FD scheme of Remark 2 (no cubic) through depth-4 passes."""
+    a, b, phi0, (eps, dt, h) = _pair(acs, (50, 132), bc, "f64", 500 + bc, 4)
+    a.set_scheme(acs.ACS_SCHEME_FEX_FD)
+    b.set_scheme(acs.ACS_SCHEME_FEX_FD)
+    a.step(11)
+    b.step(11)
+    assert np.array_equal(a.numpy(), b.numpy())
+    ref = oracle.run_fd(phi0, eps, dt, h, bc, 11, scheme=oracle.SCHEME_FEX_FD)
+    assert relerr(a.numpy(), ref) <= 1e-12
+
+
+def test_temporal2d_logged_run(acs):
+    """A logged run (E_h and max-norm every 10 steps) through depth-3 passes gives the
+    same log and state as the single-step kernel."""
+    a, b, _, _ = _pair(acs, (96, 128), BC_NEUMANN, "f32", 7, 3)
+    Ea, Ma = a.run_logged(50, 10)
+    Eb, Mb = b.run_logged(50, 10)
+    assert np.array_equal(a.numpy(), b.numpy())
+    np.testing.assert_allclose(Ea, Eb, rtol=1e-12)
+    assert np.array_equal(Ma, Mb)
+
+
+def test_temporal_unsupported_shapes(acs):
+    """Rows that are not a multiple of 16 bytes, 1D grids and depths outside 2..4 have no
+    temporally blocked kernel."""
+    s = acs.AllenCahn((33, 65), 0.02, 0.01, 1 / 65, BC_PERIODIC, "f32")
+    with pytest.raises(acs.AcsError) as e:
+        s.set_kernel(acs.ACS_KERNEL_TEMPORAL, 2)
+    assert e.value.status == acs.ACS_E_UNSUPPORTED
+    s = acs.AllenCahn((64, 64), 0.02, 0.01, 1 / 64, BC_PERIODIC, "f32")
+    with pytest.raises(acs.AcsError):
+        s.set_kernel(acs.ACS_KERNEL_TEMPORAL, 5)
+    s = acs.AllenCahn((256,), 0.02, 0.01, 1 / 256, BC_PERIODIC, "f32")
+    with pytest.raises(acs.AcsError):
+        s.set_kernel(acs.ACS_KERNEL_TEMPORAL, 2)

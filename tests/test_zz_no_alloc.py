@@ -7,7 +7,12 @@ point takes only the state and a two-double output and keeps its scratch in stat
 device memory.  Its result must match the ordinary path (acs_observe_async on a
 bound context) within the reduction tolerance of the other tests (relative 1e-12),
 on two calls in a row -- the second one reuses the static array that the first
-left filled.  This file is named to be collected last.
+left filled -- and, once the first call has looked up the array's address, a call
+must change neither torch's allocated bytes nor the device's free memory.
+
+The file name sorts last so that pytest collects it after every other test file: a
+run that stops at the first failure (-x) has then already run the rest of the suite
+when this entry point fails.  It passes alone in a fresh process as well.
 """
 import ctypes
 
@@ -57,6 +62,35 @@ def test_noalloc_matches_bound_reduction(acs, shape, bc, dtype):
         o = out.cpu().numpy()
         assert np.isfinite(o).all()
         np.testing.assert_allclose(o, r, rtol=1e-12, atol=0)
+
+
+def test_noalloc_allocates_nothing(acs):
+    """After the first call (which looks up the static array's device address), further
+    calls leave torch's allocated bytes and cudaMemGetInfo's free bytes unchanged."""
+    shape, bc = (96, 70, 64), BC_NEUMANN
+    eps, h = 0.02, 1.0 / 96
+    phi = torch.from_numpy(uniform_field(shape, -1, 1, 7)).cuda()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    L = acs.lib()
+    n = (ctypes.c_int64 * 3)(*shape)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        rc = L.acs_observe_noalloc(3, n, eps, h, bc, acs.ACS_F64, ctypes.c_void_p(phi.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), st)
+        assert rc == 0, acs.strerror(rc)
+        torch.cuda.synchronize()
+
+    call()
+    first = out.cpu().numpy().copy()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    call()
+    call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
+    assert np.array_equal(out.cpu().numpy(), first)
 
 
 def test_noalloc_rejects_bad_arguments(acs):
