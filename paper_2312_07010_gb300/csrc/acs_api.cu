@@ -126,9 +126,9 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
                 c.q[k] = (T)(kLagrangeC[k] * ak / std::pow(b, 3.0 * k + 1.0));
                 ak *= -a;
             }
-            // FP32 sums R = P - 1 and forms theta = xi + xi R: its constant term is
-            // 1/b - 1 = a/b, computed without cancellation
-            if (IncForm<T>::value) c.q[0] = (T)(a / b);
+            // the kernels sum R = P - 1 and form theta = xi + xi R: its constant term
+            // is 1/b - 1 = a/b, computed without cancellation
+            c.q[0] = (T)(a / b);
         } else {
             c.solve = kSolveNewton;
         }

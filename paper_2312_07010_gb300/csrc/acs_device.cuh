@@ -43,9 +43,9 @@ struct NewtonMax { static constexpr int value = sizeof(T) == 4 ? 4 : 6; };
 //   theta = x sum_k (-y)^k C_k,  C_k = binom(3k, k) / (2k + 1)  (1, 1, 3, 12, 55, ...),
 // convergent for y < 4/27; so theta = xi sum_k q_k (xi^2)^k with
 //   q_k = C_k (-a)^k / b^(3k+1).
-// FP64 evaluates theta = xi P(xi^2) with P = sum_k q_k x2^k; FP32 evaluates
-// theta = xi + xi R(xi^2) with R = P - 1 (its constant term q_0 - 1 = a/b), for the
-// same reason as the increment form.
+// Both precisions evaluate theta = xi + xi R(xi^2) with R = P - 1 (its constant term
+// q_0 - 1 = a/b), for the same reason as the increment form, and so that theta = +-1
+// comes out exactly at xi = +-1 (see series_root_unit).
 template <typename T>
 struct IncForm { static constexpr bool value = sizeof(T) == 4; };
 
@@ -54,7 +54,7 @@ struct Coef {
     T lam, c0, a, b, three_a;
     T m2d;        // -2 d (exact), the increment form's Laplacian weight of phi
     T na;         // -a, the increment form's reaction weight
-    T q[10];      // kSolveSeries: theta = xi * sum_k q[k] xi^(2k) (FP32: q[0] = a/b, theta = xi + xi * sum)
+    T q[10];      // kSolveSeries: theta = xi + xi * sum_k q[k] xi^(2k), q[0] = a/b
     T xi2max;     // kSolveSeries applies while xi^2 <= xi2max
     T fast2max;   // several-points fast path (tiled kernels): xi^2 bound, see roots()
     T rb, t;      // kSolveNewton: 1/b, a/b
@@ -144,33 +144,41 @@ __device__ __forceinline__ T newton_fix(T th, T xi, const Coef<T>& c) {
     return th;
 }
 
-// The truncated Lagrange series at xi (x2 = xi^2): xi P(x2), or xi + xi R(x2) in FP32.
+// The truncated Lagrange series at xi (x2 = xi^2): xi + xi R(x2), R = P - 1.
 template <typename T, int NT>
 __device__ __forceinline__ T series_eval(T xi, T x2, const Coef<T>& c) {
-    T P = c.q[NT - 1];
+    T R = c.q[NT - 1];
 #pragma unroll
-    for (int k = NT - 2; k >= 0; --k) P = dfma(P, x2, c.q[k]);
-    return IncForm<T>::value ? dfma(xi, P, xi) : xi * P;
+    for (int k = NT - 2; k >= 0; --k) R = dfma(R, x2, c.q[k]);
+    return dfma(xi, R, xi);
 }
 
 // Root of theta + (dt/2) f(theta) = xi (Remark 1), i.e. a theta^3 + b theta = xi.
 // The host picks the mode and its limits from a-priori error bounds so that the
 // fast paths are accurate to the last bit of T for |xi| <= 1.001 (Theorem 2's
 // range plus rounding); larger |xi| take the robust path.
-// x limited to [-1, 1]; NaN passes through (PTX max.NaN / min.NaN).
+// x limited to [-1, 1]; NaN passes through.  FP32: PTX max.NaN / min.NaN.  FP64: a
+// test of the high word on the integer units (it keeps the FP64 pipe, which bounds
+// the FP64 step, free): 1 <= |x| < Inf becomes +-1, anything else is kept.
 __device__ __forceinline__ float clamp_unit(float x) {
     float r;
     asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(-1.0f));
     asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(r), "f"(1.0f));
     return r;
 }
+__device__ __forceinline__ double clamp_unit(double x) {
+    const int hi = __double2hiint(x);
+    const unsigned ahi = (unsigned)hi & 0x7fffffffu;
+    if (ahi >= 0x3ff00000u && ahi < 0x7ff00000u) return __hiloint2double((hi & (int)0x80000000) | 0x3ff00000, 0);
+    return x;
+}
 
-// FP32 series solve while Theorem 2's condition holds (c.clamp): with |phi| <= 1 the
-// exact predictor obeys |xi| <= 1 (its explicit part is a convex combination), so xi
-// is limited to [-1, 1] (a no-op in exact arithmetic), and then |theta| <= 1 needs no
-// guard: the series' truncation error (<= 2^-26, chosen by the host for
-// |xi| <= 1.001) and the rounding of R stay below the 2^-24 gap above 1, so xi = +-1
-// gives +-1 exactly and |xi| < 1 gives |theta| <= 1.
+// Series solve while Theorem 2's condition holds (c.clamp): with |phi| <= 1 the exact
+// predictor obeys |xi| <= 1 (its explicit part is a convex combination), so xi is
+// limited to [-1, 1] (a no-op in exact arithmetic), and then |theta| <= 1 needs no
+// guard: the series' truncation error (<= 2^-26 FP32, 2^-55 FP64, chosen by the host
+// for |xi| <= 1.001) and the rounding of R stay below the half-ulp gap above 1
+// (2^-24, 2^-53), so xi = +-1 gives +-1 exactly and |xi| < 1 gives |theta| <= 1.
 template <typename T>
 __device__ __forceinline__ T series_root_unit(T xi, const Coef<T>& c) {
     const T xc = clamp_unit(xi);
@@ -180,7 +188,7 @@ __device__ __forceinline__ T series_root_unit(T xi, const Coef<T>& c) {
 template <typename T, int SOLVE>
 __device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
     T th;
-    if constexpr (IncForm<T>::value && SOLVE == kSolveSeries) {
+    if constexpr (SOLVE == kSolveSeries) {
         if (c.clamp) return series_root_unit(xi, c);
     }
     if (SOLVE == kSolveSeries) {

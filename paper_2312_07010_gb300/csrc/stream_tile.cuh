@@ -134,8 +134,8 @@ constexpr int kNumTileVariants = 3;
         }                                                     \
     } while (0)
 
-// Cubic root of the RPT x VX values of one thread.  FP32 with the series solve and
-// Theorem 2's condition: series_root_unit() per point.  Otherwise, with the series
+// Cubic root of the RPT x VX values of one thread.  The series solve under Theorem 2's
+// condition: series_root_unit() per point.  Otherwise, with the series
 // solve and every xi^2 <= fast2max, the series is evaluated without per-point checks
 // and (when the rounding guard is on) clamped with plain min/max: fast2max keeps |xi| <= 1 + 8 ulp,
 // where the exact root is within [-1, 1] to rounding, so this gives the same values
@@ -148,7 +148,7 @@ __device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<
         for (int i = 0; i < N; ++i) out[i] = xi[i];
         return;
     }
-    if constexpr (IncForm<T>::value && SOLVE == kSolveSeries) {
+    if constexpr (SOLVE == kSolveSeries) {
         if (c.clamp) {
 #pragma unroll
             for (int i = 0; i < N; ++i) out[i] = series_root_unit(xi[i], c);
