@@ -17,7 +17,9 @@ namespace acs {
 enum Solve : int {
     kSolveNewton = 0,  // a seed (three-term series or rational) + `newton` Newton corrections
     kSolveSeries = 1,  // SeriesTerms<T> terms of the Lagrange series, no division
-    kSolveFex = 2      // FEX-FD scheme of Remark 2: no cubic at all
+    kSolveFex = 2,     // FEX-FD scheme of Remark 2: no cubic at all
+    kSolveSeriesUnit = 3  // kSolveSeries with Theorem 2's condition known to hold (c.clamp): the
+                          // series_root_unit() path without a run-time test (temporal kernels)
 };
 template <typename T>
 struct SeriesTerms { static constexpr int value = sizeof(T) == 4 ? 5 : 9; };
@@ -188,6 +190,7 @@ __device__ __forceinline__ T series_root_unit(T xi, const Coef<T>& c) {
 template <typename T, int SOLVE>
 __device__ __forceinline__ T cubic_root(T xi, const Coef<T>& c) {
     T th;
+    if constexpr (SOLVE == kSolveSeriesUnit) return series_root_unit(xi, c);
     if constexpr (SOLVE == kSolveSeries) {
         if (c.clamp) return series_root_unit(xi, c);
     }
@@ -258,6 +261,18 @@ struct Geo {
     int64_t sy, sz;      // strides of y and z (x stride is 1)
     int64_t total;
 };
+
+// Dispatch of the temporal kernels: the series solve under Theorem 2's condition is
+// its own case (kSolveSeriesUnit), so the kernels carry no test of c.clamp.
+#define ACS_SOLVE_DISPATCH_UNIT(c, S, ...)                      \
+    do {                                                        \
+        if ((c).solve == ::acs::kSolveSeries && (c).clamp) {    \
+            constexpr int S = ::acs::kSolveSeriesUnit;          \
+            __VA_ARGS__;                                        \
+        } else {                                                \
+            ACS_SOLVE_DISPATCH((c).solve, S, __VA_ARGS__);      \
+        }                                                       \
+    } while (0)
 
 // Dispatch a runtime Solve mode to a template parameter.
 #define ACS_SOLVE_DISPATCH(mode, S, ...)                 \

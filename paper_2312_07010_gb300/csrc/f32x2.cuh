@@ -106,7 +106,7 @@ template <int SOLVE, int NP>
 __device__ __forceinline__ void roots2(const f2 (&xi)[NP], float (&out)[2 * NP], const Coef<float>& c,
                                        const PackedCoef& pc) {
     constexpr int NT = SeriesTerms<float>::value;
-    if (SOLVE == kSolveSeries && c.clamp) {
+    if (SOLVE == kSolveSeriesUnit || (SOLVE == kSolveSeries && c.clamp)) {
         // series_root_unit() on pairs
 #pragma unroll
         for (int i = 0; i < NP; ++i) {

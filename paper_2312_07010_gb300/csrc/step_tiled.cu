@@ -63,9 +63,17 @@ template <typename T>
 cudaError_t launch_step2d_tb(int bc, int depth, const T* src, T* dst, const Geo& g, const Coef<T>& c, int ych,
                              cudaStream_t st);
 
-// Temporal blocking: 2D grids whose rows are a multiple of 16 bytes, depth 2..4.
+bool step3d_tb_supported(int dtype, int depth, const Geo& g);
+template <typename T>
+cudaError_t launch_step3d_tb(int bc, int depth, const T* src, T* dst, const Geo& g, const Coef<T>& c, int zch,
+                             cudaStream_t st);
+
+// Temporal blocking: 2D grids whose rows are a multiple of 16 bytes, depth 2..4; 3D
+// FP32 grids with an even row length, depth 2 (FP64 is bound by its arithmetic pipe,
+// where fusing steps saves nothing).
 bool temporal_supported(int dims, int dtype, int depth, const Geo& g) {
     if (dims == 2) return step2d_tb_supported(dtype, depth, g);
+    if (dims == 3) return step3d_tb_supported(dtype, depth, g);
     return false;
 }
 
@@ -81,13 +89,19 @@ cudaError_t launch_step_tiled(int dims, int bc, const T* src, T* dst, const Geo&
     return cudaErrorNotSupported;
 }
 // `depth` fused steps src -> dst; a depth of 1 (the remainder of a run) is the
-// single-step tiled kernel, which rounds identically.  chunk: 16-row blocks per warp
-// (0 = chosen from the occupancy).
+// single-step tiled kernel, or the one-thread kernel where the tiled one does not
+// cover the shape (3D rows that are not a multiple of 16 bytes); all round identically.  chunk: 16-row blocks per warp
+// (2D) or z planes per CTA (3D); 0 = chosen from the occupancy.
 template <typename T>
 cudaError_t launch_step_temporal(int dims, int bc, int depth, const T* src, T* dst, const Geo& g, const Coef<T>& c,
                                  int variant, int chunk, int* err, cudaStream_t st) {
-    if (depth == 1) return launch_step_tiled<T>(dims, bc, src, dst, g, c, variant, 0, err, st);
+    if (depth == 1) {
+        if (tiled_supported(dims, sizeof(T) == 4 ? ACS_F32 : ACS_F64, g))
+            return launch_step_tiled<T>(dims, bc, src, dst, g, c, variant, 0, err, st);
+        return launch_step_naive<T>(dims, bc, src, dst, g, c, st);
+    }
     if (dims == 2) return launch_step2d_tb<T>(bc, depth, src, dst, g, c, 16 * chunk, st);
+    if (dims == 3) return launch_step3d_tb<T>(bc, depth, src, dst, g, c, chunk, st);
     return cudaErrorNotSupported;
 }
 template cudaError_t launch_step_tiled<float>(int, int, const float*, float*, const Geo&, const Coef<float>&, int,

@@ -148,6 +148,11 @@ __device__ __forceinline__ void roots(const T (&xi)[N], T (&out)[N], const Coef<
         for (int i = 0; i < N; ++i) out[i] = xi[i];
         return;
     }
+    if constexpr (SOLVE == kSolveSeriesUnit) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = series_root_unit(xi[i], c);
+        return;
+    }
     if constexpr (SOLVE == kSolveSeries) {
         if (c.clamp) {
 #pragma unroll

@@ -245,7 +245,7 @@ static cudaError_t launch_tb2d_k(int bc, const T* src, T* dst, const Geo& g, con
     using TB = Tb2<T, K>;
     const int64_t nstrips = (g.nx + TB::OW - 1) / TB::OW;
     cudaError_t e = cudaSuccess;
-    ACS_SOLVE_DISPATCH(c.solve, SV, {
+    ACS_SOLVE_DISPATCH_UNIT(c, SV, {
         auto kern = bc == 0 ? k_step2d_tb<T, 0, SV, K> : (bc == 1 ? k_step2d_tb<T, 1, SV, K> : k_step2d_tb<T, 2, SV, K>);
         if (ych <= 0) {
             int dev = 0, sms = 0, per_sm = 0;

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import BC_DIRICHLET, BC_NEUMANN, BC_PERIODIC, cfg3, dt_rule, uniform_field
+from workloads import BC_DIRICHLET, BC_NEUMANN, BC_PERIODIC, cfg2, cfg3, dt_rule, uniform_field
 
 pytestmark = pytest.mark.gpu
 
@@ -117,9 +117,57 @@ def test_temporal2d_logged_run(acs):
     assert np.array_equal(Ma, Mb)
 
 
+SHAPES_3D = [(2, 3, 4), (5, 7, 8), (9, 33, 64), (20, 70, 130), (33, 17, 12), (64, 64, 64), (70, 65, 126),
+             (7, 130, 62)]
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("shape", SHAPES_3D, ids=str)
+def test_temporal3d_bitwise_equals_single_steps(acs, shape, bc):
+    """3D FP32 at depth 2: windows smaller than the grid and larger, partial windows in
+    x and y, partial z chunks, an odd step count (passes plus one single step)."""
+    a, b, _, _ = _pair(acs, shape, bc, "f32", 600 + bc, 2)
+    assert a.get_kernel() == (acs.ACS_KERNEL_TEMPORAL, 2)
+    a.step(11)
+    b.step(11)
+    assert np.array_equal(a.numpy(), b.numpy())
+
+
+@pytest.mark.parametrize("chunk", [1, 5, 17])
+def test_temporal3d_z_chunks(acs, chunk):
+    """Explicit z chunks (1, 5, 17 planes per CTA)."""
+    a, b, _, _ = _pair(acs, (41, 60, 72), BC_DIRICHLET, "f32", 700 + chunk, 2, chunk)
+    a.step(8)
+    b.step(8)
+    assert np.array_equal(a.numpy(), b.numpy())
+
+
+def test_temporal3d_cfg2_full_grid(acs):
+    """The 512^3 Neumann grid, 10 steps at depth 2, equals the TMA-streamed single-step
+    kernel bit for bit; a logged run through it gives the same E_h log."""
+    w = cfg2("f32")
+    phi0 = w.phi0().astype(np.float32)
+    a = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    b = acs.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    a.set_kernel(acs.ACS_KERNEL_TEMPORAL, 2)
+    b.set_kernel(acs.ACS_KERNEL_TILED)
+    a.set_state(phi0)
+    b.set_state(phi0)
+    a.step(10)
+    b.step(10)
+    assert np.array_equal(a.numpy(), b.numpy())
+    a.set_state(phi0)
+    b.set_state(phi0)
+    Ea, Ma = a.run_logged(20, 10)
+    Eb, Mb = b.run_logged(20, 10)
+    assert np.array_equal(a.numpy(), b.numpy())
+    np.testing.assert_allclose(Ea, Eb, rtol=1e-12)
+    assert np.array_equal(Ma, Mb)
+
+
 def test_temporal_unsupported_shapes(acs):
-    """Rows that are not a multiple of 16 bytes, 1D grids and depths outside 2..4 have no
-    temporally blocked kernel."""
+    """Rows that are not a multiple of 16 bytes (2D) or of odd length (3D), 1D grids, 3D
+    FP64 grids and depths beyond the kernels' have no temporally blocked kernel."""
     s = acs.AllenCahn((33, 65), 0.02, 0.01, 1 / 65, BC_PERIODIC, "f32")
     with pytest.raises(acs.AcsError) as e:
         s.set_kernel(acs.ACS_KERNEL_TEMPORAL, 2)
@@ -130,3 +178,8 @@ def test_temporal_unsupported_shapes(acs):
     s = acs.AllenCahn((256,), 0.02, 0.01, 1 / 256, BC_PERIODIC, "f32")
     with pytest.raises(acs.AcsError):
         s.set_kernel(acs.ACS_KERNEL_TEMPORAL, 2)
+    for shape, dtype, depth in (((8, 8, 8), "f64", 2), ((8, 8, 9), "f32", 2), ((8, 8, 8), "f32", 3)):
+        s = acs.AllenCahn(shape, 0.02, 0.01, 1 / 8, BC_PERIODIC, dtype)
+        with pytest.raises(acs.AcsError) as e:
+            s.set_kernel(acs.ACS_KERNEL_TEMPORAL, depth)
+        assert e.value.status == acs.ACS_E_UNSUPPORTED
