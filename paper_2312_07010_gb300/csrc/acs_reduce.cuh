@@ -7,6 +7,7 @@
 #include <climits>
 
 #include "acs_device.cuh"
+#include "f2ops.cuh"
 
 namespace acs {
 
@@ -365,6 +366,52 @@ __device__ __forceinline__ void bulk_sq(F2& acc, float p) {
     const float q = wh * wh;
     const float ql = __fmaf_rn(wh, wh, -q) + 2.0f * wh * wl;
     f2_acc(acc, q, ql);
+}
+
+// The same terms for two points at once (packed lanes; the operations of each lane
+// are those of the scalar helpers above, so each lane's terms are those bits).  The
+// accumulator holds one unevaluated pair per lane.
+struct F2x2 {
+    f2 hi, lo;
+};
+struct EftConst {
+    f2 m1, two;  // -1 and 2 in both lanes
+};
+__device__ __forceinline__ EftConst eft_const() { return EftConst{f2_splat(-1.0f), f2_splat(2.0f)}; }
+
+// two_sum(a, b) per lane
+__device__ __forceinline__ F2x2 two_sum2(f2 a, f2 b) {
+    const f2 s = f2_add(a, b);
+    const f2 bb = f2_sub(s, a);
+    return F2x2{s, f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb))};
+}
+// two_sum(q, -p) per lane: (-p) - bb = -(p + bb), so the error term is
+// (q - (s - bb)) - (p + bb) with the same rounding
+__device__ __forceinline__ F2x2 two_diff2(f2 q, f2 p) {
+    const f2 s = f2_sub(q, p);
+    const f2 bb = f2_sub(s, q);
+    return F2x2{s, f2_sub(f2_sub(q, f2_sub(s, bb)), f2_add(p, bb))};
+}
+__device__ __forceinline__ void f2_acc2(F2x2& acc, f2 xh, f2 xl) {
+    const F2x2 t = two_sum2(acc.hi, xh);
+    acc.hi = t.hi;
+    acc.lo = f2_add(f2_add(acc.lo, t.lo), xl);
+}
+// the exact square of an unevaluated pair (h, l): h^2 as (sq, fma(h, h, -sq) + (2 h) l)
+__device__ __forceinline__ void sq_acc2(F2x2& acc, f2 h, f2 l, const EftConst& k) {
+    const f2 sq = f2_mul(h, h);
+    const f2 sql = f2_add(f2_fma(h, h, f2_mul(sq, k.m1)), f2_mul(f2_mul(k.two, h), l));
+    f2_acc2(acc, sq, sql);
+}
+__device__ __forceinline__ void link_sq2(F2x2& acc, f2 q, f2 p, const EftConst& k) {
+    const F2x2 d = two_diff2(q, p);
+    sq_acc2(acc, d.hi, d.lo, k);
+}
+__device__ __forceinline__ void bulk_sq2(F2x2& acc, f2 p, const EftConst& k) {
+    const f2 s2 = f2_mul(p, p);
+    const f2 s2l = f2_fma(p, p, f2_mul(s2, k.m1));
+    const F2x2 w = two_sum2(s2, k.m1);
+    sq_acc2(acc, w.hi, f2_add(w.lo, s2l), k);
 }
 
 }  // namespace acs

@@ -124,13 +124,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && RPT == 2) ? 3 : 2)
                 if (MODE == kModeEnergy) {
                     // forward links along x and y (ghost-ruled as for the step) and the
                     // links of the first unknowns to the zero Dirichlet boundary
-                    if (gyr < ny) {
+                    if (gyr < ny && colok) {  // rows are a multiple of VX: the whole vector
+                        if constexpr (std::is_same<T, float>::value) {
+                            // FP32: the four points as two packed pairs
+                            eacc.point2_pair(f2_make(cz[rr][0], cz[rr][1]), f2_make(cz[rr][1], cz[rr][2]),
+                                             f2_make(yp[0], yp[1]));
+                            eacc.point2_pair(f2_make(cz[rr][2], cz[rr][3]), f2_make(cz[rr][3], right),
+                                             f2_make(yp[2], yp[3]));
+                        } else {
 #pragma unroll
-                        for (int v = 0; v < VX; ++v) {
-                            if (gx + v >= nx) continue;
-                            const T p = cz[rr][v];
-                            eacc.point2(p, v == VX - 1 ? right : cz[rr][v + 1], yp[v]);
-                            if (BC == ACS_BC_DIRICHLET) {
+                            for (int v = 0; v < VX; ++v) eacc.point2(cz[rr][v], v == VX - 1 ? right : cz[rr][v + 1], yp[v]);
+                        }
+                        if (BC == ACS_BC_DIRICHLET) {
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) {
+                                const T p = cz[rr][v];
                                 if (gx + v == 0) eacc.ghost_link(p);
                                 if (gyr == 0) eacc.ghost_link(p);
                             }

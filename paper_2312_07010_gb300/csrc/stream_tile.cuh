@@ -43,18 +43,35 @@ __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || 
 enum StreamMode : int { kModeStep = 0, kModeEnergy = 1 };
 
 // Per-thread E_h / max-norm accumulation for the streamed kernels.  FP32 states: terms
-// are formed exactly with error-free transformations into float pairs (acs_reduce.cuh)
-// and folded into FP64 every 4 planes (at most 128 terms per pair: about 2^-41 relative
-// accumulation error); FP64 states: plain FP64 sums.  The bulk sum is of (p^2 - 1)^2
+// are formed exactly with error-free transformations into float pairs (acs_reduce.cuh;
+// two points at once on packed lanes) and folded into FP64 every 8 planes (at most 128
+// terms per pair: about 2^-41 relative accumulation error); FP64 states: FP64 sums.  The bulk sum is of (p^2 - 1)^2
 // (the 1/4 is applied by the finishing kernel), the link sum of squared differences.
 template <typename T>
 struct EnergyAcc;
 template <>
 struct EnergyAcc<float> {
     F2 fb{0.0f, 0.0f}, fl{0.0f, 0.0f};
+    // the same sums for pairs of points (two lanes each; point_pair / point2_pair)
+    F2x2 pb{f2_splat(0.0f), f2_splat(0.0f)}, pl{f2_splat(0.0f), f2_splat(0.0f)};
+    EftConst k = eft_const();
     double db = 0.0, dl = 0.0, mx = 0.0;
     float fmx = 0.0f;
     int planes = 0;
+    // two neighbouring points (lanes) p with their forward x, y (and z) neighbours
+    __device__ __forceinline__ void point_pair(f2 p, f2 xn, f2 yn, f2 zn) {
+        bulk_sq2(pb, p, k);
+        link_sq2(pl, xn, p, k);
+        link_sq2(pl, yn, p, k);
+        link_sq2(pl, zn, p, k);
+        fmx = nanmax(fmx, nanmax(fabsf(f2_lo(p)), fabsf(f2_hi(p))));
+    }
+    __device__ __forceinline__ void point2_pair(f2 p, f2 xn, f2 yn) {
+        bulk_sq2(pb, p, k);
+        link_sq2(pl, xn, p, k);
+        link_sq2(pl, yn, p, k);
+        fmx = nanmax(fmx, nanmax(fabsf(f2_lo(p)), fabsf(f2_hi(p))));
+    }
     __device__ __forceinline__ void point(float p, float xn, float yn, float zn) {
         bulk_sq(fb, p);
         link_sq(fl, xn, p);
@@ -69,14 +86,26 @@ struct EnergyAcc<float> {
         fmx = nanmax(fmx, fabsf(p));
     }
     __device__ __forceinline__ void ghost_link(float p) { link_sq(fl, 0.0f, p); }
+    // the scalar pair and the two lanes of the packed pair, summed exactly in FP32 (their
+    // high parts by TwoSum, their low parts, about 2^-24 of the highs, plainly)
+    static __device__ __forceinline__ F2 merge(F2 a, const F2x2& p) {
+        const F2 t = two_sum(f2_lo(p.hi), f2_hi(p.hi));
+        const F2 u = two_sum(a.hi, t.hi);
+        return F2{u.hi, ((a.lo + (f2_lo(p.lo) + f2_hi(p.lo))) + t.lo) + u.lo};
+    }
     __device__ __forceinline__ void fold() {
-        db += (double)fb.hi + (double)fb.lo;
-        dl += (double)fl.hi + (double)fl.lo;
+        const F2 b = merge(fb, pb), l = merge(fl, pl);
+        db += (double)b.hi + (double)b.lo;
+        dl += (double)l.hi + (double)l.lo;
         fb = F2{0.0f, 0.0f};
         fl = F2{0.0f, 0.0f};
+        pb = F2x2{f2_splat(0.0f), f2_splat(0.0f)};
+        pl = F2x2{f2_splat(0.0f), f2_splat(0.0f)};
     }
+    // fold every 8 planes: a lane then holds at most 32 bulk and 96 link terms of the
+    // 2 x 2 pairs a thread forms per plane (FP64 operations are scarce on this GPU)
     __device__ __forceinline__ void plane_done() {
-        if (++planes == 4) { fold(); planes = 0; }
+        if (++planes == 8) { fold(); planes = 0; }
     }
     __device__ __forceinline__ void finish() {
         fold();
