@@ -344,6 +344,31 @@ ACS_API int acs_batch_row_strides(const acs_batch* b, int64_t* row_strides);
 ACS_API size_t acs_batch_work_bytes(const acs_batch* b);
 ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_bytes, void* stream);
 ACS_API int acs_batch_step(acs_batch* b, int64_t n_steps);
+
+/*
+ * Launch configuration of the batched kernel (results do not depend on it: every
+ * instance stays bit-identical to its standalone run).
+ *   ctas_per_sm        CTAs of the persistent grid per SM, 0 = as many as fit
+ *                      (acs_batch_get_config then reports that number once bound)
+ *   blocks_per_ticket  consecutive blocks a CTA takes per draw, 1..16
+ *   order              0: blocks instance after instance; 1: the largest instances'
+ *                      blocks first (the small ones then fill the end of each step)
+ * acs_batch_set_config  ACS_E_INVAL for values outside those ranges.
+ * acs_batch_autotune    times every (ctas_per_sm, blocks_per_ticket in {1, 2, 4},
+ *                       order) on the bound batch with 16-step launches in which every
+ *                       step reads the state and writes the work buffer's second state
+ *                       (the state is unchanged), keeps the fastest, and records it in the tuning
+ *                       cache (see acs_autotune) under the batch's workload class:
+ *                       dtype, instance count, total unknowns, a histogram of sides in
+ *                       octaves and the boundary mix.  acs_batch_bind applies a cached
+ *                       choice for the class.  Synchronizes; *us_per_step (may be NULL)
+ *                       receives the winner's time per step.
+ *                       ACS_E_STATE before acs_batch_bind.
+ * The paper has no batched form; this tunes the launch of many copies of its 2D step.
+ */
+ACS_API int acs_batch_set_config(acs_batch* b, int ctas_per_sm, int blocks_per_ticket, int order);
+ACS_API int acs_batch_get_config(const acs_batch* b, int* ctas_per_sm, int* blocks_per_ticket, int* order);
+ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step);
 /* Per-instance E_h and max|phi| into host arrays of `count` doubles; synchronizes. */
 ACS_API int acs_batch_observe(acs_batch* b, double* h_energy, double* h_maxnorm);
 /* Testing aid for the failure path: mode 1 makes one CTA of the next batched launch

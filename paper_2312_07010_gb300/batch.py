@@ -72,6 +72,22 @@ class Batch:
         torch.cuda.synchronize()
         return self.unpack(self.phi.cpu().numpy())
 
+    def set_config(self, ctas_per_sm: int, blocks_per_ticket: int, order: int) -> None:
+        check(self.L.acs_batch_set_config(self.b, int(ctas_per_sm), int(blocks_per_ticket), int(order)),
+              "acs_batch_set_config")
+
+    def get_config(self) -> Tuple[int, int, int]:
+        v = [ctypes.c_int() for _ in range(3)]
+        check(self.L.acs_batch_get_config(self.b, *[ctypes.byref(x) for x in v]), "acs_batch_get_config")
+        return tuple(x.value for x in v)
+
+    def autotune(self) -> float:
+        """Time the launch configurations on the bound batch (state unchanged); returns
+        the winner's microseconds per step."""
+        us = ctypes.c_double()
+        check(self.L.acs_batch_autotune(self.b, ctypes.byref(us)), "acs_batch_autotune")
+        return us.value
+
     def step(self, n: int) -> None:
         check(self.L.acs_batch_step(self.b, int(n)), "acs_batch_step")
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "acs_kernels.cuh"
@@ -87,6 +88,9 @@ bool tune_cache_lookup(int dims, const int64_t* n, int bc, int dtype, int scheme
                        int* variant, int* chunk);
 void tune_cache_store(int dims, const int64_t* n, int bc, int dtype, int scheme, int kernel, int depth, int variant,
                       int chunk, double us);
+// The same for a workload class named by a string (the device is added to the key).
+bool tune_cache_lookup_class(const std::string& cls, int* v4);
+void tune_cache_store_class(const std::string& cls, const int* v4, double us);
 
 // Implemented in adjoint.cu.
 int grad_on_set_state(acs_ctx* c);

@@ -18,11 +18,15 @@
 // records ACS_E_TIMEOUT and raises an abort flag that releases every other waiter,
 // so a broken launch ends in about a second instead of hanging the GPU.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "acs_host.h"
+#include "f32x2.cuh"
 #include "stream_tile.cuh"
 #include "tma.cuh"
 
@@ -49,15 +53,16 @@ struct BlockRef {
 
 // Tile geometry of the batched kernel.  FP32: 4 rows per thread (128 x 32 blocks), 3
 // ring slots, 3 CTAs per SM; FP64: 2 rows (64 x 16 blocks), 4 slots, 2 CTAs per SM
-// (4 rows spill there).  Blocks are handed out one at a time (kChunk consecutive
-// blocks per ticket).  Each instance has one tensor-map set: main box, column box,
+// (4 rows spill there).  Blocks are handed out kch at a time (1 unless the batched
+// autotuner chose more).  Each instance has one tensor-map set: main box, column box,
 // row box, for each of the two state buffers.  Measured on the 256-instance workload
 // (FP32, GLUPS): 2 rows / 4 slots / chunks of 4: 592; 4 rows / 3 slots / chunks of 2:
 // 651; chunks of 1: 673; 4 rows / 4 slots: 615; 3 rows: 644.
 template <typename T>
 using BatchTile = Tile3<T, sizeof(T) == 4 ? 4 : 2, sizeof(T) == 4 ? 3 : 4>;
-constexpr int kChunk = 1;
 constexpr int kMapsPerInst = 6;
+constexpr int kMaxBatchChunk = 16;  // largest blocks-per-ticket setting
+constexpr int kTuneSteps = 16;      // steps per timed launch of acs_batch_autotune
 constexpr int kFenceWords = 64;  // instances whose maps a CTA remembers as acquired
 
 template <typename T>
@@ -147,7 +152,11 @@ __device__ __forceinline__ void batch_block(const T* cur, const T* colb, const T
     const int xl = lx * VX, gx = x0 + xl, r0 = RPT * ly, gy0 = y0 + r0;
     const bool neu = bc == ACS_BC_NEUMANN;
     const int lastv = n - 1 - gx;  // vector lane of column n - 1 (if in 0 .. VX - 1)
+    constexpr bool PACKED = std::is_same<T, float>::value && !EDGE;
     T cz[RPT][VX], below[VX], above[VX], xi[NP];
+    f2 xip[2 * RPT];
+    PackedCoef pc;
+    if constexpr (PACKED) pc = packed_coef(c);
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) Vec<T>::get(cur + (r0 + rr + 1) * BW + VX + xl, cz[rr]);
     Vec<T>::get(cur + r0 * BW + VX + xl, below);
@@ -194,17 +203,26 @@ __device__ __forceinline__ void batch_block(const T* cur, const T* colb, const T
                 left = cz[rr][0];
             }
         }
+        if constexpr (PACKED) {
+            // FP32 off the boundary: the same operations on pairs of points
+            f2 x2p[2];
+            predict4_2d(ym, cz[rr], yp, left, right, pc, x2p);
+            xip[2 * rr] = x2p[0];
+            xip[2 * rr + 1] = x2p[1];
+        } else {
 #pragma unroll
-        for (int v = 0; v < VX; ++v) {
-            const T xm = v == 0 ? left : cz[rr][v - 1];
-            T xp = v == VX - 1 ? right : cz[rr][v + 1];
-            if (EDGE && v == lastv) xp = neu ? cz[rr][v] : wrapx;
-            xi[rr * VX + v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
+            for (int v = 0; v < VX; ++v) {
+                const T xm = v == 0 ? left : cz[rr][v - 1];
+                T xp = v == VX - 1 ? right : cz[rr][v + 1];
+                if (EDGE && v == lastv) xp = neu ? cz[rr][v] : wrapx;
+                xi[rr * VX + v] = predictor(cz[rr][v], nsum(ym[v], yp[v], xm, xp), c);
+            }
         }
     }
     (void)TY;
     T out[NP];
-    roots<T, SOLVE, NP>(xi, out, c);
+    if constexpr (PACKED) roots2<SOLVE, 2 * RPT>(xip, out, c, pc);
+    else roots<T, SOLVE, NP>(xi, out, c);
     T* o = dst + (int64_t)gy0 * sy + gx;
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
@@ -224,14 +242,15 @@ __device__ __forceinline__ void batch_block_any(const T* cur, const T* colb, con
                                                 int64_t sy, const Coef<T>& c, const BlockRef& br) {
     constexpr int TX = BatchTile<T>::TX, TY = BatchTile<T>::TY;
     const bool edge = bc != ACS_BC_DIRICHLET && (br.x0 == 0 || br.x0 + TX >= n || br.y0 == 0 || br.y0 + TY >= n);
-    ACS_SOLVE_DISPATCH(c.solve, SV, {
+    ACS_SOLVE_DISPATCH_UNIT(c, SV, {
         if (edge) batch_block<T, SV, true>(cur, colb, rowb, dst, n, bc, sy, c, br);
         else batch_block<T, SV, false>(cur, colb, rowb, dst, n, bc, sy, c, br);
     });
 }
 
-// Persistent cooperative kernel: nsteps steps of every instance.  Per step, CTAs take
-// chunks of kChunk consecutive blocks from the step's ticket counter (so instances of
+// Persistent cooperative kernel: nsteps steps of every instance (with `fixed`, every
+// step reads A and writes B: the same work and barriers, for timing without changing A).  Per step, CTAs take
+// chunks of kch consecutive blocks from the step's ticket counter (so instances of
 // different cost balance out), stream them through the TMA ring, and meet at the grid
 // barrier.  Lane 0 of a ninth warp is the producer: it draws tickets one chunk ahead,
 // issues each block's loads into the next free slot with the block's description in
@@ -243,8 +262,8 @@ __device__ __forceinline__ void batch_block_any(const T* cur, const T* colb, con
 template <typename T>
 __global__ void __launch_bounds__(288, sizeof(T) == 4 ? 3 : 2) k_batch2d(T* A, T* B, const DevInst<T>* __restrict__ inst,
                                                  const CUtensorMap* __restrict__ maps, int count,
-                                                 const BlockRef* __restrict__ blocks, int nblocks, int nsteps,
-                                                 BarrierState* bs, int* err) {
+                                                 const BlockRef* __restrict__ blocks, int nblocks, int kch,
+                                                 int nsteps, int fixed, BarrierState* bs, int* err) {
     using TT = BatchTile<T>;
     using SM = BatchSmem<T>;
     constexpr int VX = TT::VX, S = TT::S, WARPS = 8;
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(288, sizeof(T) == 4 ? 3 : 2) k_batch2d(T* A, T
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int lane = threadIdx.x;
     const bool producer = threadIdx.y == WARPS && lane == 0;
-    const unsigned nchunks = (unsigned)((nblocks + kChunk - 1) / kChunk);
+    const unsigned nchunks = (unsigned)((nblocks + kch - 1) / kch);
     if (tid < kFenceWords) fenced[tid] = 0u;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -310,7 +329,7 @@ __global__ void __launch_bounds__(288, sizeof(T) == 4 ? 3 : 2) k_batch2d(T* A, T
             ++qi;
             return;
         }
-        const BlockRef br = blocks[(size_t)cur * kChunk + j];
+        const BlockRef br = blocks[(size_t)cur * kch + j];
         meta[s] = br;
         T* dstp = ring + (size_t)s * SLOT_ELEMS;
         unsigned char* colp = colbase + (size_t)s * SM::COL_STRIDE;
@@ -321,7 +340,7 @@ __global__ void __launch_bounds__(288, sizeof(T) == 4 ? 3 : 2) k_batch2d(T* A, T
             atomicExch(err, 2);
         } else {
             acquire_maps(br.inst);
-            const CUtensorMap* m = &maps[(size_t)br.inst * kMapsPerInst + 3 * (step & 1)];
+            const CUtensorMap* m = &maps[(size_t)br.inst * kMapsPerInst + 3 * (fixed ? 0 : (step & 1))];
             const uint32_t bytes = TT::SLOT_BYTES + SM::INST_BYTES + (br.colx >= 0 ? SM::COL_BYTES : 0u) +
                                    (br.rowy >= 0 ? SM::ROW_BYTES : 0u);
             fence_proxy_async();
@@ -332,13 +351,13 @@ __global__ void __launch_bounds__(288, sizeof(T) == 4 ? 3 : 2) k_batch2d(T* A, T
             if (br.rowy >= 0) tma_load_2d(rowp, &m[2], &full[s], xb, br.rowy);
         }
         ++qi;
-        if (++j == kChunk || (size_t)cur * kChunk + j >= (size_t)nblocks) {
+        if (++j == kch || (size_t)cur * kch + j >= (size_t)nblocks) {
             cur = pf;
             j = 0;
             if (cur < nchunks) {
                 pf = draw();
                 // the next chunk's descriptors, one block ahead of their first use
-                asm volatile("prefetch.L1 [%0];" ::"l"(blocks + (size_t)cur * kChunk));
+                asm volatile("prefetch.L1 [%0];" ::"l"(blocks + (size_t)cur * kch));
             }
         }
     };
@@ -346,7 +365,7 @@ __global__ void __launch_bounds__(288, sizeof(T) == 4 ? 3 : 2) k_batch2d(T* A, T
     int64_t q = 0;  // next sequence number to consume (the same in every consumer warp)
     bool failed = false;
     for (step = 0; step < nsteps && !failed; ++step) {
-        T* dst = (step & 1) ? A : B;
+        T* dst = (step & 1) && !fixed ? A : B;
         if (producer) {
             // other CTAs' stores of the previous step (ordered by the grid barrier)
             // before this thread's async-proxy reads of them
@@ -424,6 +443,11 @@ struct acs_batch {
     RedPartial* partials;
     double* results;
     int grid;
+    // launch configuration (acs_batch_set_config / acs_batch_autotune): CTAs per SM of
+    // the persistent grid (0 = all that fit), blocks per ticket, block order
+    int ctas, chunk, order;
+    int sms, per_sm;                  // SM count and resident CTAs per SM of the kernel
+    std::vector<BlockRef> blocks0;    // the blocks in instance order
     std::vector<std::pair<int64_t, cudaGraphExec_t>> graphs;
 };
 
@@ -451,7 +475,7 @@ void drop_graphs(acs_batch* b) {
 }
 
 template <typename T>
-cudaError_t launch_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
+cudaError_t launch_batch(acs_batch* b, int64_t nsteps, cudaStream_t st, int fixed = 0) {
     auto kern = k_batch2d<T>;
     const size_t smem = BatchSmem<T>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -461,8 +485,8 @@ cudaError_t launch_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
     const DevInst<T>* in = (const DevInst<T>*)b->dinst;
     const CUtensorMap* maps = b->maps;
     const BlockRef* blocks = b->dblocks;
-    int count = b->count, nblocks = (int)b->blocks.size(), ns = (int)nsteps;
-    void* args[] = {&A, &B, &in, &maps, &count, &blocks, &nblocks, &ns, &b->bs, &b->err};
+    int count = b->count, nblocks = (int)b->blocks.size(), kch = b->chunk, ns = (int)nsteps;
+    void* args[] = {&A, &B, &in, &maps, &count, &blocks, &nblocks, &kch, &ns, &fixed, &b->bs, &b->err};
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)b->grid);
@@ -495,6 +519,49 @@ cudaError_t enqueue_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
         done += k;
     }
     return cudaSuccess;
+}
+
+// The block list in the configured order (0: instance after instance; 1: the largest
+// instances first, so their blocks are drawn first and the small ones fill the end of
+// every step), each instance's blocks in their own order.
+void order_blocks(acs_batch* b) {
+    b->blocks = b->blocks0;
+    if (b->order == 1)
+        std::stable_sort(b->blocks.begin(), b->blocks.end(),
+                         [b](const BlockRef& x, const BlockRef& y) { return b->n[x.inst] > b->n[y.inst]; });
+}
+
+// Upload the block list and size the persistent grid for the configuration.
+cudaError_t apply_config(acs_batch* b) {
+    order_blocks(b);
+    cudaError_t e = cudaMemcpyAsync(b->dblocks, b->blocks.data(), sizeof(BlockRef) * b->blocks.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return e;
+    const int ctas = b->ctas > 0 ? std::min(b->ctas, b->per_sm) : b->per_sm;
+    const int64_t chunks = ((int64_t)b->blocks.size() + b->chunk - 1) / b->chunk;
+    b->grid = (int)std::min<int64_t>((int64_t)b->sms * ctas, chunks);
+    drop_graphs(b);
+    return cudaStreamSynchronize(b->stream);
+}
+
+// Workload class of a batch for the tuning cache: dtype, count, total unknowns, a
+// histogram of sides in octaves (log2 bins) and the boundary mix.
+std::string batch_class(const acs_batch* b) {
+    int64_t total = 0;
+    int hist[32] = {0}, bcs[3] = {0, 0, 0};
+    for (int i = 0; i < b->count; ++i) {
+        total += b->n[i] * b->n[i];
+        int k = 0;
+        while ((int64_t(2) << k) <= b->n[i] && k < 31) ++k;
+        ++hist[k];
+        ++bcs[b->bc[i]];
+    }
+    std::string key = "batch/t" + std::to_string(b->dtype) + "/c" + std::to_string(b->count) + "/u" +
+                      std::to_string(total) + "/bc" + std::to_string(bcs[0]) + "-" + std::to_string(bcs[1]) + "-" +
+                      std::to_string(bcs[2]) + "/h";
+    for (int k = 0; k < 32; ++k)
+        if (hist[k]) key += std::to_string(k) + ":" + std::to_string(hist[k]) + ",";
+    return key;
 }
 
 template <typename T>
@@ -595,6 +662,11 @@ ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, con
     }
     if (dtype == ACS_F32) fill_inst<float>(b, b->inf);
     else fill_inst<double>(b, b->ind);
+    b->blocks0 = b->blocks;
+    b->ctas = 0;
+    b->chunk = 1;
+    b->order = 0;
+    b->sms = b->per_sm = 0;
     b->bound = false;
     b->phi = b->work = b->other = nullptr;
     b->stream = b->cap = nullptr;
@@ -665,9 +737,93 @@ ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_
                                                           BatchSmem<double>::BYTES);
     }
     if (e != cudaSuccess || per_sm < 1) return ACS_E_CUDA;
-    const int64_t chunks = ((int64_t)b->blocks.size() + kChunk - 1) / kChunk;
-    b->grid = (int)std::min<int64_t>((int64_t)sms * per_sm, chunks);
+    b->sms = sms;
+    b->per_sm = per_sm;
+    // a configuration the autotuner chose for this workload class earlier
+    int v[4];
+    if (tune_cache_lookup_class(batch_class(b), v) && v[0] >= 0 && v[1] >= 1 && v[1] <= kMaxBatchChunk &&
+        (v[2] == 0 || v[2] == 1)) {
+        b->ctas = v[0];
+        b->chunk = v[1];
+        b->order = v[2];
+    }
+    if (apply_config(b) != cudaSuccess) return ACS_E_CUDA;
     b->bound = true;
+    return ACS_OK;
+}
+
+ACS_API int acs_batch_set_config(acs_batch* b, int ctas_per_sm, int blocks_per_ticket, int order) {
+    if (!b || ctas_per_sm < 0 || blocks_per_ticket < 1 || blocks_per_ticket > kMaxBatchChunk ||
+        (order != 0 && order != 1))
+        return ACS_E_INVAL;
+    b->ctas = ctas_per_sm;
+    b->chunk = blocks_per_ticket;
+    b->order = order;
+    if (!b->bound) return ACS_OK;
+    return apply_config(b) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+}
+
+ACS_API int acs_batch_get_config(const acs_batch* b, int* ctas_per_sm, int* blocks_per_ticket, int* order) {
+    if (!b) return ACS_E_INVAL;
+    if (ctas_per_sm) *ctas_per_sm = b->bound && b->ctas == 0 ? b->per_sm : b->ctas;
+    if (blocks_per_ticket) *blocks_per_ticket = b->chunk;
+    if (order) *order = b->order;
+    return ACS_OK;
+}
+
+ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step) {
+    if (!b) return ACS_E_INVAL;
+    if (!b->bound) return ACS_E_STATE;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ACS_E_CUDA;
+    const int saved[3] = {b->ctas, b->chunk, b->order};
+    int best_cfg[3] = {saved[0], saved[1], saved[2]};
+    double best = 1e300;
+    int rc = ACS_OK;
+    static const int kChunks[3] = {1, 2, 4};
+    for (int order = 0; order <= 1 && rc == ACS_OK; ++order)
+        for (int ctas = 1; ctas <= b->per_sm && rc == ACS_OK; ++ctas)
+            for (int ci = 0; ci < 3 && rc == ACS_OK; ++ci) {
+                b->ctas = ctas;
+                b->chunk = kChunks[ci];
+                b->order = order;
+                if (apply_config(b) != cudaSuccess) { rc = ACS_E_CUDA; break; }
+                // launches of kTuneSteps steps that each read phi and write the second
+                // buffer (the state is only read), with the grid barriers of a real run
+                double ms_best = 1e300;
+                for (int round = 0; round < 3; ++round) {
+                    cudaMemsetAsync(b->bs->ctr, 0, sizeof(b->bs->ctr), b->stream);
+                    cudaEventRecord(e0, b->stream);
+                    if ((b->dtype == ACS_F32 ? launch_batch<float>(b, kTuneSteps, b->stream, 1)
+                                             : launch_batch<double>(b, kTuneSteps, b->stream, 1)) != cudaSuccess)
+                        rc = ACS_E_CUDA;
+                    cudaEventRecord(e1, b->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = ACS_E_CUDA;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (round > 0) ms_best = std::min(ms_best, (double)ms / kTuneSteps);
+                }
+                if (rc == ACS_OK && ms_best < best) {
+                    best = ms_best;
+                    best_cfg[0] = ctas; best_cfg[1] = kChunks[ci]; best_cfg[2] = order;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->ctas = best_cfg[0];
+    b->chunk = best_cfg[1];
+    b->order = best_cfg[2];
+    if (apply_config(b) != cudaSuccess) rc = ACS_E_CUDA;
+    if (rc != ACS_OK) return rc;
+    int herr = 0;
+    if (cudaMemcpy(&herr, b->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ACS_E_CUDA;
+    if (herr) {
+        cudaMemset(b->err, 0, sizeof(int));
+        return ACS_E_TIMEOUT;
+    }
+    const int v[4] = {best_cfg[0], best_cfg[1], best_cfg[2], 0};
+    tune_cache_store_class(batch_class(b), v, 1e3 * best);
+    if (us_per_step) *us_per_step = 1e3 * best;
     return ACS_OK;
 }
 

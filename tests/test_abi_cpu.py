@@ -77,6 +77,23 @@ def test_noalloc_rejects_overflowing_shapes_on_host(L):
         assert L.acs_observe_noalloc(dims, arr, 0.1, 0.1, 0, 0, fake, fake, None) == -1
 
 
+def test_batch_config_validation_on_host(L):
+    """acs_batch_set_config checks its ranges before any CUDA call (the batch is not bound)."""
+    n = (ctypes.c_int64 * 2)(16, 24)
+    d = (ctypes.c_double * 2)
+    bc = (ctypes.c_int * 2)(0, 2)
+    b = ctypes.c_void_p()
+    assert L.acs_batch_create(2, n, d(0.02, 0.02), d(0.01, 0.01), d(1 / 16, 1 / 25), bc, 0, ctypes.byref(b)) >= 0
+    for bad in ((-1, 1, 0), (0, 0, 0), (0, 17, 0), (1, 1, 2)):
+        assert L.acs_batch_set_config(b, *bad) == -1, bad
+    assert L.acs_batch_set_config(b, 2, 4, 1) == 0
+    v = [ctypes.c_int() for _ in range(3)]
+    assert L.acs_batch_get_config(b, *[ctypes.byref(x) for x in v]) == 0
+    assert [x.value for x in v] == [2, 4, 1]
+    assert L.acs_batch_autotune(b, None) == -6  # not bound
+    L.acs_batch_destroy(b)
+
+
 def test_create_warns_on_step_conditions(L):
     h = 1 / 64
     eps = 8 * math.tanh(0.9) * h / math.sqrt(2)

@@ -150,3 +150,59 @@ def test_batch_full_workload(acs):
         s.step(BATCH_STEPS)
         assert np.array_equal(got[k], s.numpy()), k
         s.close()
+
+
+def _standalone(acs, inst, phi0, steps):
+    out = []
+    for k, i in enumerate(inst):
+        s = acs.AllenCahn((i.n, i.n), i.eps, i.dt, i.h, i.bc, "f32")
+        s.set_state(phi0[k])
+        s.step(steps)
+        out.append(s.numpy())
+        s.close()
+    return out
+
+
+@pytest.mark.parametrize("cfg", [(1, 1, 0), (2, 4, 1), (3, 2, 1), (0, 16, 0), (1, 3, 1)], ids=str)
+def test_batch_launch_configs_bitwise(acs, cfg):
+    """Every launch configuration (CTAs per SM, blocks per ticket, block order) gives the
+    standalone runs' bits."""
+    inst = _instances(30, 9, 8, 400)
+    b = acs.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+                  [i.bc for i in inst], "f32")
+    b.set_config(*cfg)
+    c, ch, order = b.get_config()
+    assert (ch, order) == cfg[1:] and c >= 1
+    phi0 = [i.phi0().astype(np.float32) for i in inst]
+    b.set_states(phi0)
+    b.step(9)
+    got = b.states()
+    for k, ref in enumerate(_standalone(acs, inst, phi0, 9)):
+        assert np.array_equal(got[k], ref), k
+    b.close()
+
+
+def test_batch_autotune_keeps_state_bits_and_cache(acs, tmp_path, monkeypatch):
+    """acs_batch_autotune reads the state only, its choice keeps the standalone bits, and
+    a second batch of the same workload class takes the cached choice at bind."""
+    monkeypatch.setenv("ACS_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    inst = _instances(40, 77, 16, 320)
+    args = ([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
+            [i.bc for i in inst], "f32")
+    b = acs.Batch(*args)
+    phi0 = [i.phi0().astype(np.float32) for i in inst]
+    b.set_states(phi0)
+    us = b.autotune()
+    assert us > 0
+    for k, st in enumerate(b.states()):
+        assert np.array_equal(st, phi0[k]), k
+    cfg = b.get_config()
+    assert "batch/" in (tmp_path / "tune.txt").read_text()
+    b.step(12)
+    got = b.states()
+    for k, ref in enumerate(_standalone(acs, inst, phi0, 12)):
+        assert np.array_equal(got[k], ref), k
+    b.close()
+    b2 = acs.Batch(*args)
+    assert b2.get_config() == cfg
+    b2.close()
