@@ -52,6 +52,14 @@ def _dist():
     return ws, rank, local
 
 
+def _sm_max_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -557,7 +565,8 @@ def extras(P, args):
     out["energy_pass_512cubed_f32"] = {"us": ms * 1e3, "alg_bytes": w2.numel * 4,
                                        "achieved_gbs": w2.numel * 4 / (ms * 1e-3) / 1e9,
                                        "hbm_frac": w2.numel * 4 / (ms * 1e-3) / 1e9 / peak,
-                                       "bound": "FP32 issue (exact terms: about 90 operations per unknown)"}
+                                       "bound": "FP32 issue (exact float-pair terms on packed lanes: about 42 "
+                                                "packed operations per unknown)"}
     s.close()
     del s
     torch.cuda.empty_cache()
@@ -586,6 +595,32 @@ def extras(P, args):
         s.close()
         del s, phi0
         torch.cuda.empty_cache()
+    # FP64 steps are bound by the FP64 pipe (ncu: 82-86 % busy), which retires 2 FP64
+    # operations per cycle per SM; per update the step issues 17 of them in 2D (predictor:
+    # 3 DADD, 2 DMUL, 2 DFMA; series root: 1 DMUL, 9 DFMA) and 19 in 3D (5 DADD)
+    sm_mhz = _sm_max_mhz()
+    for name, ops in (("cfg3_fp64_4096sq", 17), ("cfg2_fp64_512cubed", 19)):
+        roof = 2.0 * 152 * sm_mhz * 1e6 / ops / 1e9
+        out[name]["fp64_pipe_roof_glups"] = roof
+        out[name]["fp64_ops_per_update"] = ops
+        out[name]["fp64_pipe_roof_frac"] = out[name]["glups"] / roof
+    # the 4096^2 Dirichlet FP32 workload by kernel: single steps, then K fused steps per pass
+    w = cfg3("f32")
+    phi0 = torch.from_numpy(w.phi0().astype(np.float32)).cuda()
+    depths = {}
+    for kernel, depth in ((P.ACS_KERNEL_TILED, 1), (P.ACS_KERNEL_TEMPORAL, 2), (P.ACS_KERNEL_TEMPORAL, 3),
+                          (P.ACS_KERNEL_TEMPORAL, 4)):
+        s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+        s.set_kernel(kernel, depth)
+        s.set_state(phi0)
+        ms = _time(lambda: s.step(96), 3)
+        glups = w.numel * 96 / (ms * 1e-3) / 1e9
+        depths[f"K{depth}"] = {"glups": glups, "us_per_time_step": 1e3 * ms / 96,
+                               "hbm_frac_effective": glups * 8 / peak}
+        s.close()
+    out["cfg3_fp32_4096sq_by_depth"] = depths
+    del phi0
+    torch.cuda.empty_cache()
     # batched: 256 2D instances (seed 2), FP32, 500 steps in one persistent launch,
     # against the same instances stepped one after another as single problems
     from workloads import BATCH_STEPS, batched_instances
@@ -594,7 +629,15 @@ def extras(P, args):
                 [i.bc for i in inst], "f32")
     states = [i.phi0().astype(np.float32) for i in inst]
     b.set_states(states)
+    b.set_config(0, 1, 0)  # all resident CTAs, one block per ticket, instance order
     b.step(BATCH_STEPS)  # records the graph
+    torch.cuda.synchronize()
+    b.set_states(states)
+    ms_default = _time(lambda: b.step(BATCH_STEPS), 1)
+    us_tune = b.autotune()
+    cfg_b = b.get_config()
+    b.set_states(states)
+    b.step(BATCH_STEPS)
     torch.cuda.synchronize()
     b.set_states(states)
     ms_b = _time(lambda: b.step(BATCH_STEPS), 1)
@@ -616,7 +659,10 @@ def extras(P, args):
                                "unknowns": sum(i.n * i.n for i in inst), "steps": BATCH_STEPS,
                                "sequential_single_glups": units / (ms_s * 1e-3) / 1e9, "sequential_ms": ms_s,
                                "speedup_vs_sequential": ms_s / ms_b, "max_abs_phi": float(np.max(M)),
-                               "hbm_frac_effective": units / (ms_b * 1e-3) * 8 / (peak * 1e9)}
+                               "hbm_frac_effective": units / (ms_b * 1e-3) * 8 / (peak * 1e9),
+                               "autotuned_config": {"ctas_per_sm": cfg_b[0], "blocks_per_ticket": cfg_b[1],
+                                                    "block_order": cfg_b[2], "tuning_us_per_step": us_tune},
+                               "default_config_glups": units / (ms_default * 1e-3) / 1e9}
     del singles, b
     torch.cuda.empty_cache()
     # adjoint: 1024^2 periodic, FP32, 500 steps, checkpoints every 50

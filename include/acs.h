@@ -58,8 +58,11 @@ typedef struct acs_pipe acs_pipe;
 /* Boundary conditions (Sec. I: HN-BC, HD-BC, P-BC; matrices of Eq. Ddeltax). */
 enum { ACS_BC_PERIODIC = 0, ACS_BC_NEUMANN = 1, ACS_BC_DIRICHLET = 2 };
 
-/* State precision: FP32 state and arithmetic, or FP64.  Energy and maximum-norm
- * reductions accumulate in FP64 (compensated sums) for both. */
+/* State precision: FP32 state and arithmetic, or FP64.  The energy reduction forms
+ * every term of an FP32 state exactly (float pairs from error-free transformations)
+ * and sums them in FP64 per thread; FP64 states sum plain FP64 terms per thread (fma,
+ * no compensation).  Partial sums of threads and blocks are combined exactly (128-bit
+ * fixed point), so the result is deterministic.  The maximum norm is exact. */
 enum { ACS_F32 = 0, ACS_F64 = 1 };
 
 /* Status codes. */
@@ -84,7 +87,7 @@ enum {
     ACS_KERNEL_AUTO = 0,     /* autotuned choice, cached per problem class */
     ACS_KERNEL_NAIVE = 1,    /* one thread per unknown, neighbours via the cache hierarchy */
     ACS_KERNEL_TILED = 2,    /* shared-memory tiles (TMA-staged for d >= 2) with a one-cell halo */
-    ACS_KERNEL_TEMPORAL = 3, /* several fused steps per pass through HBM (temporal blocking) */
+    ACS_KERNEL_TEMPORAL = 3, /* several fused steps per pass through HBM (temporal blocking); see acs_set_kernel */
     ACS_KERNEL_LB = 4        /* 2d+1 stored populations: collide, then stream + solve (acs_lb_bind) */
 };
 
@@ -144,8 +147,11 @@ ACS_API int acs_set_scheme(acs_ctx* ctx, int scheme);
 
 /*
  * acs_set_kernel -- choose the kernel variant; depth is the number of fused
- * steps per pass for ACS_KERNEL_TEMPORAL (1..8) and ignored otherwise.
- * ACS_E_UNSUPPORTED if the variant does not exist for this (dims, dtype).
+ * steps per pass for ACS_KERNEL_TEMPORAL and ignored otherwise (ACS_E_INVAL outside
+ * 1..8).  Temporal blocking exists for 2D grids whose rows are a multiple of 16 bytes
+ * (depth 2..4, FP32 and FP64) and 3D FP32 grids with rows of an even length (depth
+ * 2); a run's remainder of fewer than `depth` steps takes single steps, which round
+ * identically.  ACS_E_UNSUPPORTED if the variant does not exist for this problem.
  */
 ACS_API int acs_set_kernel(acs_ctx* ctx, int kernel, int depth);
 /* The variant acs_step() uses (after autotuning, for ACS_KERNEL_AUTO). */
@@ -211,8 +217,9 @@ ACS_API int64_t acs_steps_done(const acs_ctx* ctx);
  *   E_h = h^d [ 1/4 sum_i (phi_i^2 - 1)^2 + eps^2/2 sum_links ((phi_j - phi_i)/h)^2 ],
  * where -Phi^T Lambda_{dx} Phi is written as the sum over lattice links (periodic:
  * the wrap-around link counts; Neumann: interior links only; Dirichlet: also the
- * link from each boundary unknown to the zero boundary value).  FP64,
- * compensated, deterministic.  Synchronizes the stream.
+ * link from each boundary unknown to the zero boundary value).  FP64 result; the
+ * sums are formed as described at ACS_F32 / ACS_F64 and combined exactly, so the
+ * value is deterministic.  Synchronizes the stream.
  * ACS_E_NONFINITE (value still written) if the result is not finite.
  */
 ACS_API int acs_energy(acs_ctx* ctx, double* out_host);
