@@ -271,12 +271,22 @@ def main():
                     help="only run --steps forward+backward passes of the 1024^2 adjoint workload")
     ap.add_argument("--profile-batch", action="store_true",
                     help="only set up the 256-instance batched workload and run --steps time steps")
+    ap.add_argument("--profile-2d", action="store_true",
+                    help="only run --steps time steps of the 4096^2 Dirichlet workload (--dtype, --kernel, --depth)")
+    ap.add_argument("--profile-energy", action="store_true",
+                    help="only run --steps E_h / max-norm passes over the 512^3 FP32 state")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"],
+                    help="state precision of --profile / --profile-2d")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_batch:
         return profile_batch(args)
+    if args.profile_2d:
+        return profile_2d(args)
+    if args.profile_energy:
+        return profile_energy(args)
     if args.profile_adjoint:
         return profile_adjoint(args)
     if args.profile_lines:
@@ -298,12 +308,13 @@ def main():
     import paper_2312_07010_gb300 as P
     from workloads import cfg2
     P.lib()
-    w = cfg2("f32")
-    phi0_host = torch.from_numpy(w.phi0().astype(np.float32)).pin_memory()
+    pdt = args.dtype if args.profile else "f32"
+    w = cfg2(pdt)
+    phi0_host = torch.from_numpy(w.phi0().astype(np.float32 if pdt == "f32" else np.float64)).pin_memory()
     phi0_dev = phi0_host.cuda()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32", stream=stream)
+        s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, pdt, stream=stream)
     if args.kernel:
         s.set_kernel(args.kernel, args.depth)
     if args.variant >= 0:
@@ -456,6 +467,41 @@ def main():
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
+    return 0
+
+
+def profile_2d(args):
+    import numpy as np
+    import torch
+
+    import paper_2312_07010_gb300 as P
+    from workloads import cfg3
+    w = cfg3(args.dtype)
+    s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, args.dtype)
+    if args.kernel:
+        s.set_kernel(args.kernel, args.depth)
+    s.set_state(w.phi0().astype(np.float32 if args.dtype == "f32" else np.float64))
+    s.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "cfg3_2d", "dtype": args.dtype, "kernel": s.get_kernel(), "time_steps": args.steps}))
+    return 0
+
+
+def profile_energy(args):
+    import numpy as np
+    import torch
+
+    import paper_2312_07010_gb300 as P
+    from workloads import cfg2
+    w = cfg2("f32")
+    s = P.AllenCahn(w.n, w.eps, w.dt, w.h, w.bc, "f32")
+    s.set_kernel(P.ACS_KERNEL_TILED)
+    s.set_state(w.phi0().astype(np.float32))
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    for _ in range(args.steps):
+        s.observe_async(out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "energy_512", "passes": args.steps}))
     return 0
 
 

@@ -14,9 +14,11 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "acs_host.h"
+#include "f32x2.cuh"
 #include "stream_tile.cuh"
 
 namespace acs {
@@ -41,6 +43,8 @@ __device__ __forceinline__ void line_warp(T* __restrict__ phi, const LineRec<T>&
     const int lane = threadIdx.x & 31;
     const int n = L.n, bc = L.bc;
     const Coef<T> c = L.c;
+    PackedCoef pc;
+    if constexpr (std::is_same<T, float>::value) pc = packed_coef(c);
     T* p = phi + L.off;
     T x[R];
 #pragma unroll
@@ -65,15 +69,27 @@ __device__ __forceinline__ void line_warp(T* __restrict__ phi, const LineRec<T>&
         // xi of the R points, then their roots together (the multi-point solve gives
         // the per-point cubic_root() values)
         T xi[R], out[R];
+        T sn[R];  // neighbour sums
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int gi = lane * R + r;
             const T xm = r == 0 ? (lane == 0 ? gl : up) : x[r - 1];
             T xp = r < R - 1 ? x[r + 1] : dn;
             if (gi == n - 1) xp = gr;
-            xi[r] = predictor(x[r], nsum(xm, xp), c);
+            sn[r] = nsum(xm, xp);
         }
-        roots<T, SOLVE, R>(xi, out, c);
+        if constexpr (std::is_same<T, float>::value && R % 2 == 0) {
+            // FP32: the same operations on pairs of points
+            f2 xp2[R / 2];
+#pragma unroll
+            for (int r = 0; r < R; r += 2)
+                xp2[r / 2] = predictor2(f2_make(x[r], x[r + 1]), f2_make(sn[r], sn[r + 1]), pc);
+            roots2<SOLVE, R / 2>(xp2, out, c, pc);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) xi[r] = predictor(x[r], sn[r], c);
+            roots<T, SOLVE, R>(xi, out, c);
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (lane * R + r < n) x[r] = out[r];
@@ -91,7 +107,7 @@ __global__ void __launch_bounds__(64) k_lines_warp(T* phi, const LineRec<T>* __r
     const int w = blockIdx.x * 2 + (threadIdx.x >> 5);
     if (w >= nlines) return;  // whole warps leave together
     const LineRec<T>& L = lines[ids[w]];
-    ACS_SOLVE_DISPATCH(L.c.solve, SV, line_warp<T, R, SV>(phi, L, nsteps));
+    ACS_SOLVE_DISPATCH_UNIT(L.c, SV, line_warp<T, R, SV>(phi, L, nsteps));
 }
 
 // One CTA per line in shared memory: buffers of n + 2 values (ghosts at both ends),
@@ -103,6 +119,8 @@ __device__ __forceinline__ void line_cta(T* __restrict__ phi, const LineRec<T>& 
     const int n = L.n, bc = L.bc;
     const int npad = (n + G - 1) / G * G;
     const Coef<T> c = L.c;
+    PackedCoef pc;
+    if constexpr (std::is_same<T, float>::value) pc = packed_coef(c);
     T* p = phi + L.off;
     for (int i = threadIdx.x; i < npad + 2; i += blockDim.x) {
         A[i] = i >= 1 && i <= n ? p[i - 1] : T(0);
@@ -120,9 +138,18 @@ __device__ __forceinline__ void line_cta(T* __restrict__ phi, const LineRec<T>& 
 #pragma unroll
             for (int k = 0; k < G + 2; ++k) v[k] = A[g0 + k];  // points g0 - 1 .. g0 + G
             // points past n read the ghost and the zero padding; their results are unused
+            if constexpr (std::is_same<T, float>::value) {
+                f2 xp2[G / 2];
 #pragma unroll
-            for (int k = 0; k < G; ++k) xi[k] = predictor(v[k + 1], nsum(v[k], v[k + 2]), c);
-            roots<T, SOLVE, G>(xi, out, c);
+                for (int k = 0; k < G; k += 2)
+                    xp2[k / 2] = predictor2(f2_make(v[k + 1], v[k + 2]),
+                                            f2_make(nsum(v[k], v[k + 2]), nsum(v[k + 1], v[k + 3])), pc);
+                roots2<SOLVE, G / 2>(xp2, out, c, pc);
+            } else {
+#pragma unroll
+                for (int k = 0; k < G; ++k) xi[k] = predictor(v[k + 1], nsum(v[k], v[k + 2]), c);
+                roots<T, SOLVE, G>(xi, out, c);
+            }
 #pragma unroll
             for (int k = 0; k < G; ++k)
                 if (g0 + k < n) B[g0 + k + 1] = out[k];
@@ -142,7 +169,7 @@ __global__ void __launch_bounds__(256) k_lines_cta(T* phi, const LineRec<T>* __r
     T* A = reinterpret_cast<T*>(sm);
     T* B = A + ((maxn + 3) / 4 * 4 + 2);
     const LineRec<T>& L = lines[ids[blockIdx.x]];
-    ACS_SOLVE_DISPATCH(L.c.solve, SV, line_cta<T, SV>(phi, L, nsteps, A, B));
+    ACS_SOLVE_DISPATCH_UNIT(L.c, SV, line_cta<T, SV>(phi, L, nsteps, A, B));
 }
 
 }  // namespace acs
