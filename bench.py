@@ -514,10 +514,12 @@ def profile_batch(args):
     inst = batched_instances()
     b = P.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
                 [i.bc for i in inst], "f32")
+    b.set_temporal(max(1, args.depth), 0)
     b.set_states([i.phi0().astype(np.float32) for i in inst])
     b.step(args.steps)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": "batched", "instances": len(inst), "time_steps": args.steps}))
+    print(json.dumps({"profile": "batched", "instances": len(inst), "time_steps": args.steps,
+                      "temporal_depth": b.get_temporal()[0]}))
     return 0
 
 
@@ -676,17 +678,30 @@ def extras(P, args):
     states = [i.phi0().astype(np.float32) for i in inst]
     b.set_states(states)
     b.set_config(0, 1, 0)  # all resident CTAs, one block per ticket, instance order
+    b.set_temporal(1)      # single steps
     b.step(BATCH_STEPS)  # records the graph
     torch.cuda.synchronize()
     b.set_states(states)
     ms_default = _time(lambda: b.step(BATCH_STEPS), 1)
     us_tune = b.autotune()
     cfg_b = b.get_config()
+    tcfg_b = b.get_temporal()
     b.set_states(states)
     b.step(BATCH_STEPS)
     torch.cuda.synchronize()
     b.set_states(states)
     ms_b = _time(lambda: b.step(BATCH_STEPS), 1)
+    by_depth = {}
+    for depth in (1, 2, 3, 4):
+        # the tuned single-step configuration, or the tuned unit height at each depth
+        b.set_temporal(depth, tcfg_b[1])
+        b.step(BATCH_STEPS)
+        torch.cuda.synchronize()
+        b.set_states(states)
+        ms_d = _time(lambda: b.step(BATCH_STEPS), 1)
+        by_depth[str(depth)] = {"glups": sum(i.n * i.n for i in inst) * BATCH_STEPS / (ms_d * 1e-3) / 1e9,
+                                "ms": ms_d}
+    b.set_temporal(*tcfg_b)
     units = sum(i.n * i.n for i in inst) * BATCH_STEPS
     E, M = b.observe()
     singles = []
@@ -707,7 +722,9 @@ def extras(P, args):
                                "speedup_vs_sequential": ms_s / ms_b, "max_abs_phi": float(np.max(M)),
                                "hbm_frac_effective": units / (ms_b * 1e-3) * 8 / (peak * 1e9),
                                "autotuned_config": {"ctas_per_sm": cfg_b[0], "blocks_per_ticket": cfg_b[1],
-                                                    "block_order": cfg_b[2], "tuning_us_per_step": us_tune},
+                                                    "block_order": cfg_b[2], "temporal_depth": tcfg_b[0],
+                                                    "rows_per_unit": tcfg_b[1], "tuning_us_per_step": us_tune},
+                               "by_temporal_depth": by_depth,
                                "default_config_glups": units / (ms_default * 1e-3) / 1e9}
     del singles, b
     torch.cuda.empty_cache()

@@ -362,27 +362,52 @@ ACS_API int acs_batch_step(acs_batch* b, int64_t n_steps);
  *                      blocks first (the small ones then fill the end of each step)
  * acs_batch_set_config  ACS_E_INVAL for values outside those ranges.
  * acs_batch_autotune    times every (ctas_per_sm, blocks_per_ticket in {1, 2, 4},
- *                       order) on the bound batch with 16-step launches in which every
- *                       step reads the state and writes the work buffer's second state
- *                       (the state is unchanged), keeps the fastest, and records it in the tuning
- *                       cache (see acs_autotune) under the batch's workload class:
- *                       dtype, instance count, total unknowns, a histogram of sides in
- *                       octaves and the boundary mix.  acs_batch_bind applies a cached
- *                       choice for the class.  Synchronizes; *us_per_step (may be NULL)
- *                       receives the winner's time per step.
- *                       ACS_E_STATE before acs_batch_bind.
+ *                       order) of the single-step kernel and, where the batch can use
+ *                       temporal blocking, every (depth 2..4, rows_per_unit in {32, 64,
+ *                       128}, order) of the temporally blocked kernel, on the bound batch
+ *                       with launches of about 16 steps in which every step (pass) reads
+ *                       the state and writes the work buffer's second state (the state
+ *                       is unchanged); keeps the fastest (the single-step kernel's best
+ *                       configuration stays set for the steps a temporal block leaves
+ *                       over) and records it in the tuning cache (see acs_autotune) under
+ *                       the batch's workload class: dtype, instance count, total
+ *                       unknowns, a histogram of sides in octaves and the boundary mix.
+ *                       acs_batch_bind applies a cached choice for the class.
+ *                       Synchronizes; *us_per_step (may be NULL) receives the winner's
+ *                       time per step.  ACS_E_STATE before acs_batch_bind.
  * The paper has no batched form; this tunes the launch of many copies of its 2D step.
  */
 ACS_API int acs_batch_set_config(acs_batch* b, int ctas_per_sm, int blocks_per_ticket, int order);
 ACS_API int acs_batch_get_config(const acs_batch* b, int* ctas_per_sm, int* blocks_per_ticket, int* order);
 ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step);
+
+/*
+ * Temporal blocking of the batched form: K = depth steps of Eq. IE-FD per pass
+ * through HBM, in one persistent launch for all passes of an acs_batch_step call
+ * (nsteps / K passes, then nsteps % K single steps).  Each instance is cut into units
+ * of a 120-column strip by a chunk of at most rows_per_unit rows (balanced over the
+ * side); a unit recomputes K cells of halo at each side, so its state after a pass is
+ * bit-identical to K single steps.  Units of a pass wait (bounded) only for their own
+ * instance's previous pass, not for a grid barrier.
+ *   depth          1 = the single-step kernel only; 2..4
+ *   rows_per_unit  0 = the default (64), else 16 .. 2^20
+ * acs_batch_set_temporal  ACS_E_INVAL outside those ranges; ACS_E_UNSUPPORTED for
+ *                         depth >= 2 on an FP64 batch (the FP64 step is bound by the
+ *                         FP64 pipe, not by HBM).  Applies on the next acs_batch_step;
+ *                         needs no rebinding.
+ * acs_batch_get_temporal  the depth and rows per unit in effect (either may be NULL).
+ * Results do not depend on the setting.  The paper has no batched form.
+ */
+ACS_API int acs_batch_set_temporal(acs_batch* b, int depth, int rows_per_unit);
+ACS_API int acs_batch_get_temporal(const acs_batch* b, int* depth, int* rows_per_unit);
 /* Per-instance E_h and max|phi| into host arrays of `count` doubles; synchronizes. */
 ACS_API int acs_batch_observe(acs_batch* b, double* h_energy, double* h_maxnorm);
-/* Testing aid for the failure path: mode 1 makes one CTA of the next batched launch
- * skip its arrival at the first step barrier, so the other CTAs' bounded waits
- * (about one second) expire, the launch ends early, and the next acs_batch_observe
- * returns ACS_E_TIMEOUT (which also clears the fault state); mode 0 disarms it.  No
- * GPU fault is involved. */
+/* Testing aid for the failure path: mode 1 makes one CTA of the next single-step
+ * batched launch skip its arrival at the first step barrier (with temporal blocking:
+ * the completion of the launch's first unit goes uncounted), so the other CTAs'
+ * (warps') bounded waits (about one second) expire, the launch ends early, and the
+ * next acs_batch_observe returns ACS_E_TIMEOUT (which also clears the fault state);
+ * mode 0 disarms it.  No GPU fault is involved. */
 ACS_API int acs_batch_inject_fault(acs_batch* b, int mode);
 ACS_API void acs_batch_destroy(acs_batch* b);
 

@@ -26,23 +26,12 @@
 #include <vector>
 
 #include "acs_host.h"
+#include "batch.cuh"
 #include "f32x2.cuh"
 #include "stream_tile.cuh"
 #include "tma.cuh"
 
 namespace acs {
-
-// One instance as the kernel sees it; copied into shared memory with each block.
-template <typename T>
-struct alignas(16) DevInst {
-    int64_t off;  // first element of the instance in the packed state
-    int n;        // side (x fastest)
-    int ld;       // row stride in elements (a 16-byte multiple)
-    int bc;
-    int pad;
-    Coef<T> c;
-};
-static_assert(sizeof(DevInst<float>) % 16 == 0 && sizeof(DevInst<double>) % 16 == 0, "bulk-copy size");
 
 // One block of one instance.  colx / rowy: where a periodic instance's wrapped
 // column / row for this block is fetched from when the main box does not hold it
@@ -62,7 +51,7 @@ template <typename T>
 using BatchTile = Tile3<T, sizeof(T) == 4 ? 4 : 2, sizeof(T) == 4 ? 3 : 4>;
 constexpr int kMapsPerInst = 6;
 constexpr int kMaxBatchChunk = 16;  // largest blocks-per-ticket setting
-constexpr int kTuneSteps = 16;      // steps per timed launch of acs_batch_autotune
+constexpr int kTuneSteps = 16;      // steps per timed launch of acs_batch_autotune (about as many in passes)
 constexpr int kFenceWords = 64;  // instances whose maps a CTA remembers as acquired
 
 template <typename T>
@@ -80,14 +69,6 @@ struct BatchSmem {
     static constexpr uint32_t OFF_INST = OFF_ROW + TT::S * ROW_STRIDE;
     static constexpr uint32_t OFF_META = OFF_INST + TT::S * INST_STRIDE;
     static constexpr size_t BYTES = 128 + OFF_META + TT::S * sizeof(BlockRef);
-};
-
-struct BarrierState {
-    unsigned count;   // arrivals in the current phase
-    unsigned gen;     // phase counter
-    int abort;        // set by a waiter that gave up: everyone leaves
-    int inject;       // testing aid: 1 = the last CTA skips one arrival
-    unsigned ctr[4];  // chunk tickets of step s in ctr[s & 3] (zeroed before each launch)
 };
 
 // Returns false (and the CTA must leave) if the barrier was aborted or timed out.
@@ -448,6 +429,16 @@ struct acs_batch {
     int ctas, chunk, order;
     int sms, per_sm;                  // SM count and resident CTAs per SM of the kernel
     std::vector<BlockRef> blocks0;    // the blocks in instance order
+    // temporal blocking (acs_batch_set_temporal): depth (1 = the single-step kernel
+    // only), rows per unit (0 = kDefaultTbRows), whether the batch can use the
+    // temporally blocked kernel (FP32), its unit list and persistent grid
+    int tdepth, trows;
+    bool tok;
+    int64_t tcap;                     // units the work buffer has room for
+    std::vector<TbUnit> tunits;
+    TbUnit* dunits;
+    unsigned* ddone;
+    int tgrid;
     std::vector<std::pair<int64_t, cudaGraphExec_t>> graphs;
 };
 
@@ -467,7 +458,12 @@ size_t off_blocks(const acs_batch* b) {
 size_t off_bar(const acs_batch* b) { return off_blocks(b) + al(sizeof(BlockRef) * b->blocks.size()); }
 size_t off_part(const acs_batch* b) { return off_bar(b) + kA; }
 size_t off_res(const acs_batch* b) { return off_part(b) + al(sizeof(RedPartial) * kMaxRedBlocks); }
-size_t total_bytes(const acs_batch* b) { return off_res(b) + al(sizeof(double) * 2 * (size_t)b->count); }
+size_t off_units(const acs_batch* b) { return off_res(b) + al(sizeof(double) * 2 * (size_t)b->count); }
+size_t off_done(const acs_batch* b) { return off_units(b) + al(sizeof(TbUnit) * (size_t)b->tcap); }
+size_t total_bytes(const acs_batch* b) { return off_done(b) + al(sizeof(unsigned) * (size_t)b->count); }
+
+constexpr int kDefaultTbRows = 64;         // rows per unit of the temporally blocked kernel by default
+constexpr int64_t kMaxTbUnits = 1 << 22;   // room reserved for units at most
 
 void drop_graphs(acs_batch* b) {
     for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
@@ -501,9 +497,37 @@ cudaError_t launch_batch(acs_batch* b, int64_t nsteps, cudaStream_t st, int fixe
     return cudaLaunchKernelExC(&cfg, (const void*)kern, args);
 }
 
-// One launch advances nsteps; the packed state starts in phi and, after an even
-// number of steps, ends there (an odd count ends with one device copy back).
+// npasses passes of the temporally blocked kernel (fixed: every pass reads phi and
+// writes the second buffer), with fresh ticket and completion counters.
+cudaError_t launch_tb(acs_batch* b, int64_t npasses, cudaStream_t st, int fixed = 0) {
+    cudaError_t e = cudaMemsetAsync(b->bs->ctr, 0, sizeof(b->bs->ctr), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ddone, 0, sizeof(unsigned) * (size_t)b->count, st);
+    if (e != cudaSuccess) return e;
+    return launch_batch_tb(b->tdepth, (float*)b->phi, (float*)b->other, (const DevInst<float>*)b->dinst,
+                           b->dunits, (int)b->tunits.size(), (int)npasses, fixed, b->bs, b->ddone, b->err, b->tgrid,
+                           st);
+}
+
+// Launches that advance nsteps; the packed state starts in phi and ends there (a
+// launch that leaves it in the second buffer is followed by one device copy back).
+// With temporal blocking, nsteps / K passes of K steps run first (one launch, unless
+// the ticket count needs more), then the remaining nsteps % K single steps.
 cudaError_t enqueue_batch(acs_batch* b, int64_t nsteps, cudaStream_t st) {
+    if (b->tdepth >= 2 && nsteps >= b->tdepth) {
+        const int64_t K = b->tdepth;
+        const int64_t max_passes = std::max<int64_t>(1, ((int64_t)1 << 30) / (int64_t)b->tunits.size());
+        for (int64_t left = nsteps / K; left > 0;) {
+            const int64_t p = std::min(left, max_passes);
+            cudaError_t e = launch_tb(b, p, st);
+            if (e != cudaSuccess) return e;
+            if (p & 1) {
+                e = cudaMemcpyAsync(b->phi, b->other, (size_t)b->numel * b->esize, cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return e;
+            }
+            left -= p;
+        }
+        nsteps %= K;
+    }
     const int64_t chunk_max = 1 << 20;
     for (int64_t done = 0; done < nsteps;) {
         const int64_t k = std::min(chunk_max, nsteps - done);
@@ -531,7 +555,30 @@ void order_blocks(acs_batch* b) {
                          [b](const BlockRef& x, const BlockRef& y) { return b->n[x.inst] > b->n[y.inst]; });
 }
 
-// Upload the block list and size the persistent grid for the configuration.
+// Unit list of the temporally blocked kernel: instances in the configured order (0: as
+// given; 1: the largest first), each strip after strip, a strip's chunks of rows down
+// it (balanced chunks of at most the configured rows); sets DevInst::tbunits.
+void build_tb_units(acs_batch* b) {
+    b->tunits.clear();
+    const int rows = b->trows > 0 ? b->trows : kDefaultTbRows;
+    std::vector<int> idx(b->count);
+    for (int i = 0; i < b->count; ++i) idx[i] = i;
+    if (b->order == 1) std::stable_sort(idx.begin(), idx.end(), [b](int x, int y) { return b->n[x] > b->n[y]; });
+    for (int i : idx) {
+        const int n = (int)b->n[i];
+        const int strips = (n + kBatchTbCols - 1) / kBatchTbCols;
+        const int chunks0 = (n + rows - 1) / rows;
+        const int ych = (n + chunks0 - 1) / chunks0;
+        const int chunks = (n + ych - 1) / ych;
+        for (int st = 0; st < strips; ++st)
+            for (int ck = 0; ck < chunks; ++ck)
+                b->tunits.push_back(TbUnit{i, st, ck * ych, std::min(n, (ck + 1) * ych)});
+        b->inf[i].tbunits = strips * chunks;
+    }
+}
+
+// Upload the block list (and with temporal blocking the unit list and the instances'
+// unit counts) and size the persistent grids for the configuration.
 cudaError_t apply_config(acs_batch* b) {
     order_blocks(b);
     cudaError_t e = cudaMemcpyAsync(b->dblocks, b->blocks.data(), sizeof(BlockRef) * b->blocks.size(),
@@ -540,6 +587,19 @@ cudaError_t apply_config(acs_batch* b) {
     const int ctas = b->ctas > 0 ? std::min(b->ctas, b->per_sm) : b->per_sm;
     const int64_t chunks = ((int64_t)b->blocks.size() + b->chunk - 1) / b->chunk;
     b->grid = (int)std::min<int64_t>((int64_t)b->sms * ctas, chunks);
+    if (b->tdepth >= 2) {
+        build_tb_units(b);
+        if ((int64_t)b->tunits.size() > b->tcap) return cudaErrorInvalidValue;
+        const int per = batch_tb_per_sm(b->tdepth);
+        if (per < 1) return cudaErrorInvalidConfiguration;
+        b->tgrid = b->sms * per;
+        e = cudaMemcpyAsync(b->dunits, b->tunits.data(), sizeof(TbUnit) * b->tunits.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->dinst, b->inf.data(), sizeof(DevInst<float>) * (size_t)b->count,
+                                cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return e;
+    }
     drop_graphs(b);
     return cudaStreamSynchronize(b->stream);
 }
@@ -667,6 +727,24 @@ ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, con
     b->chunk = 1;
     b->order = 0;
     b->sms = b->per_sm = 0;
+    // temporal blocking: FP32 batches whose instances all use the series root
+    b->tdepth = 1;
+    b->trows = 0;
+    b->tok = false;
+    b->tcap = 0;
+    b->tgrid = 0;
+    b->dunits = nullptr;
+    b->ddone = nullptr;
+    if (dtype == ACS_F32) {
+        // room for the units of the shortest chunks
+        int64_t cap = 0;
+        for (int i = 0; i < count; ++i)
+            cap += (n[i] + kBatchTbCols - 1) / kBatchTbCols * ((n[i] + kMinBatchRows - 1) / kMinBatchRows);
+        if (cap <= kMaxTbUnits) {
+            b->tok = true;
+            b->tcap = cap;
+        }
+    }
     b->bound = false;
     b->phi = b->work = b->other = nullptr;
     b->stream = b->cap = nullptr;
@@ -708,6 +786,8 @@ ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_
     b->err = (int*)((char*)b->bs + 64);
     b->partials = (RedPartial*)(b->work + off_part(b));
     b->results = (double*)(b->work + off_res(b));
+    b->dunits = (TbUnit*)(b->work + off_units(b));
+    b->ddone = (unsigned*)(b->work + off_done(b));
     std::vector<CUtensorMap> maps;
     const bool enc = b->dtype == ACS_F32 ? encode_maps<float>(b, maps) : encode_maps<double>(b, maps);
     if (!enc) return ACS_E_UNSUPPORTED;
@@ -742,10 +822,15 @@ ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_
     // a configuration the autotuner chose for this workload class earlier
     int v[4];
     if (tune_cache_lookup_class(batch_class(b), v) && v[0] >= 0 && v[1] >= 1 && v[1] <= kMaxBatchChunk &&
-        (v[2] == 0 || v[2] == 1)) {
+        (v[2] == 0 || v[2] == 1) && v[3] >= 0) {
         b->ctas = v[0];
         b->chunk = v[1];
         b->order = v[2];
+        const int depth = v[3] & 15, rows = v[3] >> 4;
+        if (depth >= 2 && depth <= kMaxBatchDepth && b->tok && rows >= kMinBatchRows && rows <= (1 << 20)) {
+            b->tdepth = depth;
+            b->trows = rows;
+        }
     }
     if (apply_config(b) != cudaSuccess) return ACS_E_CUDA;
     b->bound = true;
@@ -763,6 +848,24 @@ ACS_API int acs_batch_set_config(acs_batch* b, int ctas_per_sm, int blocks_per_t
     return apply_config(b) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
 }
 
+ACS_API int acs_batch_set_temporal(acs_batch* b, int depth, int rows_per_unit) {
+    if (!b || depth < 1 || depth > kMaxBatchDepth || rows_per_unit < 0 ||
+        (rows_per_unit > 0 && rows_per_unit < kMinBatchRows) || rows_per_unit > (1 << 20))
+        return ACS_E_INVAL;
+    if (depth >= 2 && !b->tok) return ACS_E_UNSUPPORTED;
+    b->tdepth = depth;
+    b->trows = rows_per_unit;
+    if (!b->bound) return ACS_OK;
+    return apply_config(b) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
+}
+
+ACS_API int acs_batch_get_temporal(const acs_batch* b, int* depth, int* rows_per_unit) {
+    if (!b) return ACS_E_INVAL;
+    if (depth) *depth = b->tdepth;
+    if (rows_per_unit) *rows_per_unit = b->trows > 0 ? b->trows : kDefaultTbRows;
+    return ACS_OK;
+}
+
 ACS_API int acs_batch_get_config(const acs_batch* b, int* ctas_per_sm, int* blocks_per_ticket, int* order) {
     if (!b) return ACS_E_INVAL;
     if (ctas_per_sm) *ctas_per_sm = b->bound && b->ctas == 0 ? b->per_sm : b->ctas;
@@ -776,43 +879,83 @@ ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step) {
     if (!b->bound) return ACS_E_STATE;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ACS_E_CUDA;
-    const int saved[3] = {b->ctas, b->chunk, b->order};
-    int best_cfg[3] = {saved[0], saved[1], saved[2]};
-    double best = 1e300;
     int rc = ACS_OK;
+    // Microseconds per step of the current configuration: the best of two launches
+    // (after one untimed) that each read phi and write the second buffer (the state is
+    // only read), kTuneSteps single steps with their grid barriers, or the passes of
+    // the temporally blocked kernel that cover about as many steps.
+    auto time_config = [&]() -> double {
+        if (apply_config(b) != cudaSuccess) {
+            rc = ACS_E_CUDA;
+            return 1e300;
+        }
+        const int64_t passes = b->tdepth >= 2 ? std::max(1, kTuneSteps / b->tdepth) : 0;
+        const int64_t steps = b->tdepth >= 2 ? passes * b->tdepth : kTuneSteps;
+        double best_ms = 1e300;
+        for (int round = 0; round < 3; ++round) {
+            cudaError_t e = cudaSuccess;
+            if (b->tdepth < 2) e = cudaMemsetAsync(b->bs->ctr, 0, sizeof(b->bs->ctr), b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) {
+                if (b->tdepth >= 2) e = launch_tb(b, passes, b->stream, 1);
+                else if (b->dtype == ACS_F32) e = launch_batch<float>(b, kTuneSteps, b->stream, 1);
+                else e = launch_batch<double>(b, kTuneSteps, b->stream, 1);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = ACS_E_CUDA;
+                return 1e300;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (round > 0) best_ms = std::min(best_ms, (double)ms / (double)steps);
+        }
+        return best_ms;
+    };
+    // the single-step kernel: order x CTAs per SM x blocks per ticket
+    int ss[3] = {b->ctas, b->chunk, b->order};
+    double ss_best = 1e300;
     static const int kChunks[3] = {1, 2, 4};
+    b->tdepth = 1;
     for (int order = 0; order <= 1 && rc == ACS_OK; ++order)
         for (int ctas = 1; ctas <= b->per_sm && rc == ACS_OK; ++ctas)
             for (int ci = 0; ci < 3 && rc == ACS_OK; ++ci) {
                 b->ctas = ctas;
                 b->chunk = kChunks[ci];
                 b->order = order;
-                if (apply_config(b) != cudaSuccess) { rc = ACS_E_CUDA; break; }
-                // launches of kTuneSteps steps that each read phi and write the second
-                // buffer (the state is only read), with the grid barriers of a real run
-                double ms_best = 1e300;
-                for (int round = 0; round < 3; ++round) {
-                    cudaMemsetAsync(b->bs->ctr, 0, sizeof(b->bs->ctr), b->stream);
-                    cudaEventRecord(e0, b->stream);
-                    if ((b->dtype == ACS_F32 ? launch_batch<float>(b, kTuneSteps, b->stream, 1)
-                                             : launch_batch<double>(b, kTuneSteps, b->stream, 1)) != cudaSuccess)
-                        rc = ACS_E_CUDA;
-                    cudaEventRecord(e1, b->stream);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = ACS_E_CUDA;
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (round > 0) ms_best = std::min(ms_best, (double)ms / kTuneSteps);
-                }
-                if (rc == ACS_OK && ms_best < best) {
-                    best = ms_best;
-                    best_cfg[0] = ctas; best_cfg[1] = kChunks[ci]; best_cfg[2] = order;
+                const double ms = time_config();
+                if (rc == ACS_OK && ms < ss_best) {
+                    ss_best = ms;
+                    ss[0] = ctas; ss[1] = kChunks[ci]; ss[2] = order;
                 }
             }
+    // the temporally blocked kernel: depth x rows per unit x order
+    int tb[3] = {1, 0, 0};
+    double tb_best = 1e300;
+    static const int kRows[3] = {32, 64, 128};
+    if (b->tok)
+        for (int depth = 2; depth <= kMaxBatchDepth && rc == ACS_OK; ++depth)
+            for (int ri = 0; ri < 3 && rc == ACS_OK; ++ri)
+                for (int order = 0; order <= 1 && rc == ACS_OK; ++order) {
+                    b->tdepth = depth;
+                    b->trows = kRows[ri];
+                    b->order = order;
+                    const double ms = time_config();
+                    if (rc == ACS_OK && ms < tb_best) {
+                        tb_best = ms;
+                        tb[0] = depth; tb[1] = kRows[ri]; tb[2] = order;
+                    }
+                }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->ctas = best_cfg[0];
-    b->chunk = best_cfg[1];
-    b->order = best_cfg[2];
+    // the single-step configuration stays for the steps a temporal block leaves over
+    b->ctas = ss[0];
+    b->chunk = ss[1];
+    const bool use_tb = tb_best < ss_best;
+    b->order = use_tb ? tb[2] : ss[2];
+    b->tdepth = use_tb ? tb[0] : 1;
+    b->trows = use_tb ? tb[1] : 0;
     if (apply_config(b) != cudaSuccess) rc = ACS_E_CUDA;
     if (rc != ACS_OK) return rc;
     int herr = 0;
@@ -821,7 +964,8 @@ ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step) {
         cudaMemset(b->err, 0, sizeof(int));
         return ACS_E_TIMEOUT;
     }
-    const int v[4] = {best_cfg[0], best_cfg[1], best_cfg[2], 0};
+    const double best = use_tb ? tb_best : ss_best;
+    const int v[4] = {b->ctas, b->chunk, b->order, use_tb ? b->tdepth + 16 * b->trows : 0};
     tune_cache_store_class(batch_class(b), v, 1e3 * best);
     if (us_per_step) *us_per_step = 1e3 * best;
     return ACS_OK;
