@@ -64,9 +64,13 @@ __device__ __forceinline__ void predict4_3d(const float (&zm)[4], const float (&
     xi[1] = predictor2(f2_make(z[2], z[3]), f2_add(f2_add(a1, b1), sx1), pc);
 }
 
+// arcp() of both lanes (the approximate reciprocal has no packed form).
+__device__ __forceinline__ f2 arcp2(f2 x) { return f2_make(arcp(f2_lo(x)), arcp(f2_hi(x))); }
+
 // roots() for FP32 points held as NP pairs: with the series solve, series_root_unit()
 // on pairs while Theorem 2's condition holds, else the fast path (every xi^2 <=
-// fast2max) on pairs with the per-point clamp; any other case unpacks and takes
+// fast2max) on pairs with the per-point clamp; with the Newton solve, roots()' fast
+// path (seed, c.newton corrections, clamp) on pairs; any other case unpacks and takes
 // roots()' scalar path, which gives the same values.
 template <int SOLVE, int NP>
 __device__ __forceinline__ void roots2(const f2 (&xi)[NP], float (&out)[2 * NP], const Coef<float>& c,
@@ -103,6 +107,63 @@ __device__ __forceinline__ void roots2(const f2 (&xi)[NP], float (&out)[2 * NP],
                 for (int k = NT - 2; k >= 0; --k) R = f2_fma(R, x2[i], pc.q[k]);
                 const f2 th = f2_fma(xi[i], R, xi[i]);
                 float lo = f2_lo(th), hi = f2_hi(th);
+                if (c.clamp) {
+                    lo = fminf(fmaxf(lo, -1.0f), 1.0f);
+                    hi = fminf(fmaxf(hi, -1.0f), 1.0f);
+                }
+                out[2 * i] = lo;
+                out[2 * i + 1] = hi;
+            }
+            return;
+        }
+    }
+    if (SOLVE == kSolveNewton) {
+        // the operations of roots()' Newton fast path, two points per instruction:
+        // seed, corrections theta -= p / p' (residual() in its FP32 form
+        // a (theta^3 - theta) + (theta - xi)), clamp; the same tests decide the path
+        const f2 rb = f2_splat(c.rb), t = f2_splat(c.t), a = f2_splat(c.a), b = f2_splat(c.b);
+        const f2 three_a = f2_splat(c.three_a), one = f2_splat(1.0f), three = f2_splat(3.0f);
+        f2 th[NP];
+        bool ok;
+        if (c.seed == 0) {
+            float my = 0.0f, m2 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const f2 x = f2_mul(xi[i], rb);
+                const f2 y = f2_mul(f2_mul(t, x), x);
+                const f2 x2 = f2_mul(xi[i], xi[i]);
+                my = nanmax(my, nanmax(f2_lo(y), f2_hi(y)));
+                m2 = nanmax(m2, nanmax(f2_lo(x2), f2_hi(x2)));
+                const f2 u = f2_mul(y, pc.m1);  // -y
+                th[i] = f2_mul(x, f2_fma(u, f2_fma(three, u, one), one));
+            }
+            ok = my <= c.ymax && m2 <= c.fast2max;
+        } else {
+            float m2 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const f2 x2 = f2_mul(xi[i], xi[i]);
+                m2 = nanmax(m2, nanmax(f2_lo(x2), f2_hi(x2)));
+                th[i] = f2_mul(xi[i], arcp2(f2_fma(a, x2, b)));
+            }
+            ok = m2 <= c.xi2max && m2 <= c.fast2max;
+        }
+        if (ok) {
+#pragma unroll
+            for (int k = 0; k < NewtonMax<float>::value; ++k) {
+                if (k < c.newton) {
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        const f2 th2 = f2_mul(th[i], th[i]);
+                        const f2 p = f2_fma(a, f2_fma(th2, th[i], f2_mul(th[i], pc.m1)), f2_sub(th[i], xi[i]));
+                        const f2 dp = f2_fma(three_a, th2, b);
+                        th[i] = f2_fma(f2_mul(p, pc.m1), arcp2(dp), th[i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                float lo = f2_lo(th[i]), hi = f2_hi(th[i]);
                 if (c.clamp) {
                     lo = fminf(fmaxf(lo, -1.0f), 1.0f);
                     hi = fminf(fmaxf(hi, -1.0f), 1.0f);
