@@ -514,9 +514,8 @@ def profile_batch(args):
     inst = batched_instances()
     b = P.Batch([i.n for i in inst], [i.eps for i in inst], [i.dt for i in inst], [i.h for i in inst],
                 [i.bc for i in inst], "f32")
-    if args.depth > 1:
-        b.set_config(0, 1, 1)  # largest instances first, as the autotuner picks for this workload
-    b.set_temporal(max(1, args.depth), 0)
+    # largest instances first, as the autotuner picks for this workload
+    b.set_temporal(max(1, args.depth), 0, 1 if args.depth > 1 else 0)
     b.set_states([i.phi0().astype(np.float32) for i in inst])
     b.step(args.steps)
     torch.cuda.synchronize()
@@ -695,8 +694,8 @@ def extras(P, args):
     ms_b = _time(lambda: b.step(BATCH_STEPS), 1)
     by_depth = {}
     for depth in (1, 2, 3, 4):
-        # the tuned single-step configuration, or the tuned unit height at each depth
-        b.set_temporal(depth, tcfg_b[1])
+        # the tuned single-step configuration, or the tuned unit height and order at each depth
+        b.set_temporal(depth, tcfg_b[1], tcfg_b[2])
         b.step(BATCH_STEPS)
         torch.cuda.synchronize()
         b.set_states(states)
@@ -725,7 +724,8 @@ def extras(P, args):
                                "hbm_frac_effective": units / (ms_b * 1e-3) * 8 / (peak * 1e9),
                                "autotuned_config": {"ctas_per_sm": cfg_b[0], "blocks_per_ticket": cfg_b[1],
                                                     "block_order": cfg_b[2], "temporal_depth": tcfg_b[0],
-                                                    "rows_per_unit": tcfg_b[1], "tuning_us_per_step": us_tune},
+                                                    "rows_per_unit": tcfg_b[1], "unit_order": tcfg_b[2],
+                                                    "tuning_us_per_step": us_tune},
                                "by_temporal_depth": by_depth,
                                "default_config_glups": units / (ms_default * 1e-3) / 1e9}
     del singles, b

@@ -391,15 +391,18 @@ ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step);
  * instance's previous pass, not for a grid barrier.
  *   depth          1 = the single-step kernel only; 2..4
  *   rows_per_unit  0 = the default (64), else 16 .. 2^20
+ *   order          0: units instance after instance; 1: the largest instances' units
+ *                  first (the single-step kernel keeps its own order, acs_batch_set_config)
  * acs_batch_set_temporal  ACS_E_INVAL outside those ranges; ACS_E_UNSUPPORTED for
  *                         depth >= 2 on an FP64 batch (the FP64 step is bound by the
  *                         FP64 pipe, not by HBM).  Applies on the next acs_batch_step;
  *                         needs no rebinding.
- * acs_batch_get_temporal  the depth and rows per unit in effect (either may be NULL).
+ * acs_batch_get_temporal  the depth, rows per unit and unit order in effect (any may be
+ *                         NULL).
  * Results do not depend on the setting.  The paper has no batched form.
  */
-ACS_API int acs_batch_set_temporal(acs_batch* b, int depth, int rows_per_unit);
-ACS_API int acs_batch_get_temporal(const acs_batch* b, int* depth, int* rows_per_unit);
+ACS_API int acs_batch_set_temporal(acs_batch* b, int depth, int rows_per_unit, int order);
+ACS_API int acs_batch_get_temporal(const acs_batch* b, int* depth, int* rows_per_unit, int* order);
 /* Per-instance E_h and max|phi| into host arrays of `count` doubles; synchronizes. */
 ACS_API int acs_batch_observe(acs_batch* b, double* h_energy, double* h_maxnorm);
 /* Testing aid for the failure path: mode 1 makes one CTA of the next single-step

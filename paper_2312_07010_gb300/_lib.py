@@ -71,8 +71,8 @@ SIGNATURES = {
     "acs_batch_set_config": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
     "acs_batch_get_config": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "acs_batch_autotune": (_c.c_int, [_vp, _dp]),
-    "acs_batch_set_temporal": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
-    "acs_batch_get_temporal": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "acs_batch_set_temporal": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
+    "acs_batch_get_temporal": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "acs_batch_observe": (_c.c_int, [_vp, _dp, _dp]),
     "acs_batch_inject_fault": (_c.c_int, [_vp, _c.c_int]),
     "acs_batch_destroy": (None, [_vp]),

@@ -81,13 +81,15 @@ class Batch:
         check(self.L.acs_batch_get_config(self.b, *[ctypes.byref(x) for x in v]), "acs_batch_get_config")
         return tuple(x.value for x in v)
 
-    def set_temporal(self, depth: int, rows_per_unit: int = 0) -> None:
+    def set_temporal(self, depth: int, rows_per_unit: int = 0, order: int = 0) -> None:
         """K = depth steps per pass through HBM (1: single steps); units of at most
-        rows_per_unit rows (0: the library's default)."""
-        check(self.L.acs_batch_set_temporal(self.b, int(depth), int(rows_per_unit)), "acs_batch_set_temporal")
+        rows_per_unit rows (0: the library's default), in instance order (0) or the
+        largest instances first (1)."""
+        check(self.L.acs_batch_set_temporal(self.b, int(depth), int(rows_per_unit), int(order)),
+              "acs_batch_set_temporal")
 
-    def get_temporal(self) -> Tuple[int, int]:
-        v = [ctypes.c_int() for _ in range(2)]
+    def get_temporal(self) -> Tuple[int, int, int]:
+        v = [ctypes.c_int() for _ in range(3)]
         check(self.L.acs_batch_get_temporal(self.b, *[ctypes.byref(x) for x in v]), "acs_batch_get_temporal")
         return tuple(x.value for x in v)
 

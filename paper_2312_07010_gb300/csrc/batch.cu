@@ -432,7 +432,7 @@ struct acs_batch {
     // temporal blocking (acs_batch_set_temporal): depth (1 = the single-step kernel
     // only), rows per unit (0 = kDefaultTbRows), whether the batch can use the
     // temporally blocked kernel (FP32), its unit list and persistent grid
-    int tdepth, trows;
+    int tdepth, trows, torder;  // torder: unit order, as `order` for the blocks
     bool tok;
     int64_t tcap;                     // units the work buffer has room for
     std::vector<TbUnit> tunits;
@@ -555,15 +555,15 @@ void order_blocks(acs_batch* b) {
                          [b](const BlockRef& x, const BlockRef& y) { return b->n[x.inst] > b->n[y.inst]; });
 }
 
-// Unit list of the temporally blocked kernel: instances in the configured order (0: as
-// given; 1: the largest first), each strip after strip, a strip's chunks of rows down
+// Unit list of the temporally blocked kernel: instances in its own configured order (0:
+// as given; 1: the largest first), each strip after strip, a strip's chunks of rows down
 // it (balanced chunks of at most the configured rows); sets DevInst::tbunits.
 void build_tb_units(acs_batch* b) {
     b->tunits.clear();
     const int rows = b->trows > 0 ? b->trows : kDefaultTbRows;
     std::vector<int> idx(b->count);
     for (int i = 0; i < b->count; ++i) idx[i] = i;
-    if (b->order == 1) std::stable_sort(idx.begin(), idx.end(), [b](int x, int y) { return b->n[x] > b->n[y]; });
+    if (b->torder == 1) std::stable_sort(idx.begin(), idx.end(), [b](int x, int y) { return b->n[x] > b->n[y]; });
     for (int i : idx) {
         const int n = (int)b->n[i];
         const int strips = (n + kBatchTbCols - 1) / kBatchTbCols;
@@ -730,6 +730,7 @@ ACS_API int acs_batch_create(int count, const int64_t* n, const double* eps, con
     // temporal blocking: FP32 batches whose instances all use the series root
     b->tdepth = 1;
     b->trows = 0;
+    b->torder = 0;
     b->tok = false;
     b->tcap = 0;
     b->tgrid = 0;
@@ -826,10 +827,12 @@ ACS_API int acs_batch_bind(acs_batch* b, void* d_phi, void* d_work, size_t work_
         b->ctas = v[0];
         b->chunk = v[1];
         b->order = v[2];
-        const int depth = v[3] & 15, rows = v[3] >> 4;
+        // fourth field: depth | unit order << 3 | rows << 4 (0: single steps)
+        const int depth = v[3] & 7, torder = (v[3] >> 3) & 1, rows = v[3] >> 4;
         if (depth >= 2 && depth <= kMaxBatchDepth && b->tok && rows >= kMinBatchRows && rows <= (1 << 20)) {
             b->tdepth = depth;
             b->trows = rows;
+            b->torder = torder;
         }
     }
     if (apply_config(b) != cudaSuccess) return ACS_E_CUDA;
@@ -848,21 +851,24 @@ ACS_API int acs_batch_set_config(acs_batch* b, int ctas_per_sm, int blocks_per_t
     return apply_config(b) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
 }
 
-ACS_API int acs_batch_set_temporal(acs_batch* b, int depth, int rows_per_unit) {
+ACS_API int acs_batch_set_temporal(acs_batch* b, int depth, int rows_per_unit, int order) {
     if (!b || depth < 1 || depth > kMaxBatchDepth || rows_per_unit < 0 ||
-        (rows_per_unit > 0 && rows_per_unit < kMinBatchRows) || rows_per_unit > (1 << 20))
+        (rows_per_unit > 0 && rows_per_unit < kMinBatchRows) || rows_per_unit > (1 << 20) ||
+        (order != 0 && order != 1))
         return ACS_E_INVAL;
     if (depth >= 2 && !b->tok) return ACS_E_UNSUPPORTED;
     b->tdepth = depth;
     b->trows = rows_per_unit;
+    b->torder = order;
     if (!b->bound) return ACS_OK;
     return apply_config(b) == cudaSuccess ? ACS_OK : ACS_E_CUDA;
 }
 
-ACS_API int acs_batch_get_temporal(const acs_batch* b, int* depth, int* rows_per_unit) {
+ACS_API int acs_batch_get_temporal(const acs_batch* b, int* depth, int* rows_per_unit, int* order) {
     if (!b) return ACS_E_INVAL;
     if (depth) *depth = b->tdepth;
     if (rows_per_unit) *rows_per_unit = b->trows > 0 ? b->trows : kDefaultTbRows;
+    if (order) *order = b->torder;
     return ACS_OK;
 }
 
@@ -940,7 +946,7 @@ ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step) {
                 for (int order = 0; order <= 1 && rc == ACS_OK; ++order) {
                     b->tdepth = depth;
                     b->trows = kRows[ri];
-                    b->order = order;
+                    b->torder = order;
                     const double ms = time_config();
                     if (rc == ACS_OK && ms < tb_best) {
                         tb_best = ms;
@@ -952,10 +958,11 @@ ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step) {
     // the single-step configuration stays for the steps a temporal block leaves over
     b->ctas = ss[0];
     b->chunk = ss[1];
+    b->order = ss[2];
     const bool use_tb = tb_best < ss_best;
-    b->order = use_tb ? tb[2] : ss[2];
     b->tdepth = use_tb ? tb[0] : 1;
     b->trows = use_tb ? tb[1] : 0;
+    b->torder = use_tb ? tb[2] : 0;
     if (apply_config(b) != cudaSuccess) rc = ACS_E_CUDA;
     if (rc != ACS_OK) return rc;
     int herr = 0;
@@ -965,7 +972,7 @@ ACS_API int acs_batch_autotune(acs_batch* b, double* us_per_step) {
         return ACS_E_TIMEOUT;
     }
     const double best = use_tb ? tb_best : ss_best;
-    const int v[4] = {b->ctas, b->chunk, b->order, use_tb ? b->tdepth + 16 * b->trows : 0};
+    const int v[4] = {b->ctas, b->chunk, b->order, use_tb ? b->tdepth | b->torder << 3 | b->trows << 4 : 0};
     tune_cache_store_class(batch_class(b), v, 1e3 * best);
     if (us_per_step) *us_per_step = 1e3 * best;
     return ACS_OK;

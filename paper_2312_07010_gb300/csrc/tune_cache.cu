@@ -3,7 +3,8 @@
 // where <key> names the device (name and SM count) and the class: for a single problem
 // dims, n, bc, dtype and scheme, with <kernel> <depth> <variant> <chunk>; for a batch
 // its workload class (acs_batch_autotune), with <ctas per SM> <blocks per ticket>
-// <block order> 0.
+// <block order> and 0 for single steps, else depth | unit order << 3 | rows per unit << 4
+// of the temporally blocked kernel.
 // The file is $ACS_TUNE_CACHE, else $HOME/.cache/acs_tune.txt; missing or
 // unreadable files simply mean "not cached".  Later lines win.
 #include <cstdio>

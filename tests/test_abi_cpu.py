@@ -100,26 +100,26 @@ def test_batch_temporal_validation_on_host(L):
     n = (ctypes.c_int64 * 2)(16, 24)
     d = (ctypes.c_double * 2)
     bc = (ctypes.c_int * 2)(0, 2)
-    v = [ctypes.c_int() for _ in range(2)]
+    v = [ctypes.c_int() for _ in range(3)]
     b = ctypes.c_void_p()
     assert L.acs_batch_create(2, n, d(0.02, 0.02), d(0.01, 0.01), d(1 / 16, 1 / 25), bc, 0, ctypes.byref(b)) >= 0
-    for bad in ((0, 0), (5, 0), (2, -1), (2, 8), (4, (1 << 20) + 1)):
+    for bad in ((0, 0, 0), (5, 0, 0), (2, -1, 0), (2, 8, 0), (4, (1 << 20) + 1, 0), (2, 0, 2), (2, 0, -1)):
         assert L.acs_batch_set_temporal(b, *bad) == -1, bad
     assert L.acs_batch_get_temporal(b, *[ctypes.byref(x) for x in v]) == 0
-    assert [x.value for x in v] == [1, 64]
-    for depth, rows in ((2, 16), (3, 0), (4, 4096), (1, 0)):
-        assert L.acs_batch_set_temporal(b, depth, rows) == 0
+    assert [x.value for x in v] == [1, 64, 0]
+    for depth, rows, order in ((2, 16, 1), (3, 0, 0), (4, 4096, 1), (1, 0, 0)):
+        assert L.acs_batch_set_temporal(b, depth, rows, order) == 0
         assert L.acs_batch_get_temporal(b, *[ctypes.byref(x) for x in v]) == 0
-        assert [x.value for x in v] == [depth, rows or 64]
+        assert [x.value for x in v] == [depth, rows or 64, order]
     L.acs_batch_destroy(b)
     # FP64: the temporally blocked kernel is FP32 only
     assert L.acs_batch_create(2, n, d(0.02, 0.02), d(0.01, 0.01), d(1 / 16, 1 / 25), bc, 1, ctypes.byref(b)) >= 0
-    assert L.acs_batch_set_temporal(b, 2, 0) == -7
-    assert L.acs_batch_set_temporal(b, 1, 0) == 0
+    assert L.acs_batch_set_temporal(b, 2, 0, 0) == -7
+    assert L.acs_batch_set_temporal(b, 1, 0, 0) == 0
     L.acs_batch_destroy(b)
     # an instance on the Newton root (a time step beyond the series' range, Remark 1)
     assert L.acs_batch_create(2, n, d(0.02, 0.02), d(0.01, 1.9), d(1 / 16, 1 / 25), bc, 0, ctypes.byref(b)) >= 0
-    assert L.acs_batch_set_temporal(b, 2, 0) == 0
+    assert L.acs_batch_set_temporal(b, 2, 0, 1) == 0
     L.acs_batch_destroy(b)
 
 

@@ -47,7 +47,7 @@ def _ragged_batch():
 def _run(acs, args, phi0, steps, depth=1, rows=0, order=0):
     b = acs.Batch(*args, "f32")
     b.set_config(0, 1, order)
-    b.set_temporal(depth, rows)
+    b.set_temporal(depth, rows, order)
     assert b.get_temporal()[0] == depth
     b.set_states(phi0)
     b.step(steps)
