@@ -632,8 +632,11 @@ def extras(P, args):
         glups = w.numel * nsteps / (ms * 1e-3) / 1e9
         esz = 4 if w.dtype == "f32" else 8
         k, d = s.get_kernel()
+        rmode, rsplit = ctypes.c_int(), ctypes.c_int()
+        P.check(P.lib().acs_get_root(s.ctx, ctypes.byref(rmode), ctypes.byref(rsplit)), "acs_get_root")
         out[name] = {"glups": glups, "ms_per_time_step": ms / nsteps, "hbm_frac_effective": glups * 2 * esz / peak,
-                     "kernel": k, "depth": d}
+                     "kernel": k, "depth": d, "root": {0: "newton", 1: "series", 2: "none"}[rmode.value],
+                     "series_fp32_tail": bool(rsplit.value)}
         if name == "cfg1_fp64_128sq":
             # the configuration as stated: 1000 steps with E_h and max|phi| every 10
             def logged():
@@ -646,9 +649,11 @@ def extras(P, args):
         torch.cuda.empty_cache()
     # FP64 steps are bound by the FP64 pipe (ncu: 82-86 % busy), which retires 2 FP64
     # operations per cycle per SM; per update the step issues 17 of them in 2D (predictor:
-    # 3 DADD, 2 DMUL, 2 DFMA; series root: 1 DMUL, 9 DFMA) and 19 in 3D (5 DADD)
+    # 3 DADD, 2 DMUL, 2 DFMA; series root: 1 DMUL, 9 DFMA) and 19 in 3D (5 DADD), two fewer
+    # where the series sums its last three terms in FP32 (acs_get_root)
     sm_mhz = _sm_max_mhz()
     for name, ops in (("cfg3_fp64_4096sq", 17), ("cfg2_fp64_512cubed", 19)):
+        ops -= 2 if out[name]["series_fp32_tail"] else 0
         roof = 2.0 * 152 * sm_mhz * 1e6 / ops / 1e9
         out[name]["fp64_pipe_roof_glups"] = roof
         out[name]["fp64_ops_per_update"] = ops

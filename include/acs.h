@@ -158,6 +158,19 @@ ACS_API int acs_set_kernel(acs_ctx* ctx, int kernel, int depth);
 ACS_API int acs_get_kernel(const acs_ctx* ctx, int* kernel, int* depth);
 
 /*
+ * acs_get_root -- how the step solves the cubic of Remark 1 (Eq. root) for this context,
+ * as the host chose it from a-priori error bounds at create / set_scheme time:
+ *   *mode   ACS_ROOT_NEWTON (seeded Newton corrections), ACS_ROOT_SERIES (truncated
+ *           Lagrange series), ACS_ROOT_NONE (FEX-FD: no cubic)
+ *   *split  FP64 series only: 1 when its terms of order xi^13 and beyond are summed in
+ *           FP32 (their effect on theta is bounded by 2^-58 for every xi the series
+ *           takes), 0 otherwise.
+ * Either pointer may be NULL.  ACS_E_INVAL for a NULL context.
+ */
+enum { ACS_ROOT_NEWTON = 0, ACS_ROOT_SERIES = 1, ACS_ROOT_NONE = 2 };
+ACS_API int acs_get_root(const acs_ctx* ctx, int* mode, int* split);
+
+/*
  * Collide-and-stream (population) form, Sec. II: Eqs. (fieq-Fi), (fneq), (RLB),
  * (pine).  A DdQ(2d+1) lattice keeps 2d+1 populations per node; one step collides
  * every node into g_k = w_k phi - ((1 - s) w_1 / s)(phi(y + c_k dt) - phi(y))

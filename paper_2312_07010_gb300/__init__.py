@@ -9,7 +9,7 @@ from . import build
 from ._lib import (ACS_BC_DIRICHLET, ACS_BC_NEUMANN, ACS_BC_PERIODIC, ACS_E_CUDA, ACS_E_INVAL,
                    ACS_E_NOMEM, ACS_E_NONFINITE, ACS_E_STATE, ACS_E_TIMEOUT, ACS_E_UNSUPPORTED, ACS_F32, ACS_F64,
                    ACS_KERNEL_AUTO, ACS_KERNEL_NAIVE, ACS_KERNEL_TEMPORAL, ACS_KERNEL_TILED,
-                   ACS_SCHEME_FEX_FD, ACS_SCHEME_RLB_MIE_FD, SIGNATURES, AcsError, check, lib,
+                   ACS_ROOT_NEWTON, ACS_ROOT_NONE, ACS_ROOT_SERIES, ACS_SCHEME_FEX_FD, ACS_SCHEME_RLB_MIE_FD, SIGNATURES, AcsError, check, lib,
                    lib_path, strerror)
 
 __all__ = [
@@ -18,7 +18,7 @@ __all__ = [
     "ACS_E_INVAL", "ACS_E_CUDA", "ACS_E_NOMEM", "ACS_E_TIMEOUT", "ACS_E_NONFINITE", "ACS_E_STATE",
     "ACS_E_UNSUPPORTED",
     "ACS_KERNEL_AUTO", "ACS_KERNEL_NAIVE", "ACS_KERNEL_TILED", "ACS_KERNEL_TEMPORAL",
-    "ACS_SCHEME_RLB_MIE_FD", "ACS_SCHEME_FEX_FD",
+    "ACS_SCHEME_RLB_MIE_FD", "ACS_SCHEME_FEX_FD", "ACS_ROOT_NEWTON", "ACS_ROOT_SERIES", "ACS_ROOT_NONE",
     "AllenCahn", "AllenCahnFunction", "allen_cahn", "Batch", "Lines", "Pipeline", "dt_max",
 ]
 

@@ -19,6 +19,7 @@ ACS_E_INVAL, ACS_E_CUDA, ACS_E_NOMEM, ACS_E_TIMEOUT = -1, -2, -3, -4
 ACS_E_NONFINITE, ACS_E_STATE, ACS_E_UNSUPPORTED = -5, -6, -7
 ACS_KERNEL_AUTO, ACS_KERNEL_NAIVE, ACS_KERNEL_TILED, ACS_KERNEL_TEMPORAL, ACS_KERNEL_LB = 0, 1, 2, 3, 4
 ACS_SCHEME_RLB_MIE_FD, ACS_SCHEME_FEX_FD = 0, 1
+ACS_ROOT_NEWTON, ACS_ROOT_SERIES, ACS_ROOT_NONE = 0, 1, 2
 
 # every function include/acs.h declares: name -> (restype, argtypes)
 _c = ctypes
@@ -37,6 +38,7 @@ SIGNATURES = {
     "acs_set_scheme": (_c.c_int, [_vp, _c.c_int]),
     "acs_set_kernel": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
     "acs_get_kernel": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "acs_get_root": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "acs_num_variants": (_c.c_int, []),
     "acs_set_variant": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
     "acs_get_variant": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),

@@ -147,6 +147,23 @@ Coef<T> make_coef(int dims, double lam, double dt, int scheme, bool mp_ok) {
     const double ulp1 = sizeof(T) == 4 ? std::ldexp(1.0, -23) : std::ldexp(1.0, -52);
     c.clamp_hi = (T)(1.0 + 16.0 * ulp1);
     c.clamp = mp_ok ? 1 : 0;
+    // FP64 series: the terms k >= kSeriesSplit of R in FP32 when that moves theta by at
+    // most 2^-58 for every xi the series takes (|xi| <= 1 under Theorem 2's clamp, else
+    // xi^2 <= xi2max).  theta = xi + xi x2^5 T with T the tail; per term the truncated
+    // x2 (2^-23 per power), the FP32 coefficient and the Horner roundings (2^-24 each)
+    // stay below (NT - kSeriesSplit + 2) 2^-23 of the term's size.
+    if (sizeof(T) == 8 && c.solve == kSolveSeries) {
+        const int nt = SeriesTerms<T>::value;
+        const double xm2 = c.clamp ? 1.0 : (double)c.xi2max;
+        double bound = 0.0;
+        for (int k = kSeriesSplit; k < nt; ++k)
+            bound += std::fabs((double)c.q[k]) * std::pow(xm2, k + 0.5);
+        bound *= (nt - kSeriesSplit + 2) * std::ldexp(1.0, -23);
+        if (nt - kSeriesSplit <= 4 && std::isfinite(bound) && bound <= std::ldexp(1.0, -58)) {
+            c.split = 1;
+            for (int k = kSeriesSplit; k < nt; ++k) c.qf[k - kSeriesSplit] = (float)c.q[k];
+        }
+    }
     // fast path of the tiled kernels: the series range, and with the rounding guard
     // on, |xi| <= 1 + 8 ulp (exact root within [-1, 1] up to rounding)
     if (c.solve == kSolveSeries) {
@@ -668,6 +685,15 @@ ACS_API int acs_get_kernel(const acs_ctx* c, int* kernel, int* depth) {
     if (!c) return ACS_E_INVAL;
     if (kernel) *kernel = c->kernel;
     if (depth) *depth = c->depth;
+    return ACS_OK;
+}
+
+ACS_API int acs_get_root(const acs_ctx* c, int* mode, int* split) {
+    if (!c) return ACS_E_INVAL;
+    static_assert(kSolveNewton == ACS_ROOT_NEWTON && kSolveSeries == ACS_ROOT_SERIES && kSolveFex == ACS_ROOT_NONE,
+                  "root modes");
+    if (mode) *mode = c->dtype == ACS_F32 ? c->cf.solve : c->cd.solve;
+    if (split) *split = c->dtype == ACS_F32 ? c->cf.split : c->cd.split;
     return ACS_OK;
 }
 

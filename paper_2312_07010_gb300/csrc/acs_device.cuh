@@ -66,7 +66,15 @@ struct Coef {
     T clamp_hi;   // 1 + 16 ulp: overshoots up to this are rounding and go back to +-1
     int clamp;    // 1: apply that rounding guard (set only when Theorem 2's condition holds)
     int solve;    // the Solve mode this context uses
+    int split;    // FP64 series: 1 = terms k >= kSeriesSplit of R in FP32 (series_eval)
+    float qf[4];  // those terms' coefficients q[kSeriesSplit ..] rounded to FP32 (3 used)
 };
+
+// FP64 series terms from this index on may be summed in FP32: the host allows it
+// (Coef::split) only where their whole contribution to theta, times the FP32 error
+// factor, stays below 2^-58 -- a small fraction of theta's own rounding -- and the
+// FP64 pipe, which bounds the FP64 step, then runs 2 of the 8 Horner steps fewer.
+constexpr int kSeriesSplit = 6;
 
 // 32-bit shared-memory address of a generic pointer into shared memory.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -147,8 +155,38 @@ __device__ __forceinline__ T newton_fix(T th, T xi, const Coef<T>& c) {
 }
 
 // The truncated Lagrange series at xi (x2 = xi^2): xi + xi R(x2), R = P - 1.
+// x >= 0 (x = xi^2) as a float on the integer units, the mantissa truncated (relative
+// error below 2^-23) and values below 2^-126 flushed to +0.  NaN gives some finite
+// value; the FP64 operations that also take x then carry the NaN.
+__device__ __forceinline__ float nonneg_f64_to_f32(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)(hi >> 20) - 896;                       // 1023 - 127
+    const unsigned m = __funnelshift_l(lo, hi, 3) & 0x7fffffu;  // top 23 of the 52 mantissa bits
+    return e <= 0 ? 0.0f : __uint_as_float(((unsigned)e << 23) | m);
+}
+// A normal float as a double on the integer units (exact); zero and subnormals give
+// a signed zero.
+__device__ __forceinline__ double f32_to_f64_int(float t) {
+    const unsigned u = __float_as_uint(t), mag = u & 0x7fffffffu;
+    if (mag < 0x00800000u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(u << 29));
+}
+
 template <typename T, int NT>
 __device__ __forceinline__ T series_eval(T xi, T x2, const Coef<T>& c) {
+    if constexpr (sizeof(T) == 8 && NT > kSeriesSplit && NT - kSeriesSplit <= 4) {
+        if (c.split) {
+            // the tail q[6] + q[7] x2 + q[8] x2^2 in FP32, the rest of the Horner scheme in FP64
+            const float x2f = nonneg_f64_to_f32(x2);
+            float t = c.qf[NT - 1 - kSeriesSplit];
+#pragma unroll
+            for (int k = NT - 2; k >= kSeriesSplit; --k) t = __fmaf_rn(t, x2f, c.qf[k - kSeriesSplit]);
+            T R = f32_to_f64_int(t);
+#pragma unroll
+            for (int k = kSeriesSplit - 1; k >= 0; --k) R = dfma(R, x2, c.q[k]);
+            return dfma(xi, R, xi);
+        }
+    }
     T R = c.q[NT - 1];
 #pragma unroll
     for (int k = NT - 2; k >= 0; --k) R = dfma(R, x2, c.q[k]);

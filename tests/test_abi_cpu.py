@@ -266,3 +266,78 @@ def test_pipe_host_logic(L):
     L.acs_destroy(ctx)
     L.acs_pipe_destroy(p)
     L.acs_pipe_destroy(None)
+
+
+def _root(L, dims, n, eps, dt, h, bc, dtype):
+    rc, ctx = _create(L, dims, n, eps, dt, h, bc, dtype)
+    assert rc >= 0
+    mode, split = ctypes.c_int(), ctypes.c_int()
+    assert L.acs_get_root(ctx, ctypes.byref(mode), ctypes.byref(split)) == 0
+    L.acs_destroy(ctx)
+    return mode.value, split.value
+
+
+def test_fp64_series_split_decisions(L):
+    """The stated FP64 workloads take the series with its FP32 tail (512^3 Neumann, 4096^2
+    Dirichlet), the 128^2 periodic one the Newton root; FP32 contexts never split."""
+    assert L.acs_get_root(None, None, None) == -1
+    assert _root(L, 3, (512, 512, 512), 0.01, 0.005685895945577131, 1 / 512, 1, 1) == (1, 1)
+    assert _root(L, 2, (4096, 4096), 0.005, 0.0017157758860686684, 2 / 4097, 2, 1) == (1, 1)
+    assert _root(L, 2, (128, 128), 0.02, 0.0274658203125, 1 / 128, 0, 1) == (0, 0)
+    assert _root(L, 3, (512, 512, 512), 0.01, 0.005685895945577131, 1 / 512, 1, 0) == (1, 0)
+    # FEX-FD has no cubic
+    rc, ctx = _create(L, 2, (64, 64), 0.02, 0.001, 1 / 64, 0, 1)
+    assert L.acs_set_scheme(ctx, 1) == 0
+    mode = ctypes.c_int()
+    assert L.acs_get_root(ctx, ctypes.byref(mode), None) == 0 and mode.value == 2
+    L.acs_destroy(ctx)
+
+
+def _tail_error(dt, xs):
+    """Largest |xi x2^6 (T32 - T)| over xs: T = sum_{k>=6} q_k x2^(k-6) evaluated exactly
+    (mpmath) from the FP64 coefficients and the FP64 x2 = xi^2, T32 as the FP64 kernels
+    form it -- x2 truncated to FP32 on the integer units, FP32 coefficients, FP32 Horner
+    (emulated: each fma exact in FP64, then rounded to FP32)."""
+    import numpy as np
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 200
+    C = [1, 1, 3, 12, 55, 273, 1428, 7752, 43263]
+    a = 0.5 * dt
+    b = 1.0 - a
+    q = [C[k] * (-a) ** k / b ** (3 * k + 1) for k in range(9)]  # q[0] is not used here
+    qf = [np.float32(q[k]) for k in (6, 7, 8)]
+    worst = 0.0
+    for xi in xs:
+        x2 = float(np.float64(xi) * np.float64(xi))
+        u = np.array([x2]).view(np.uint64)[0]
+        hi, lo = int(u >> np.uint64(32)), int(u & np.uint64(0xFFFFFFFF))
+        e = (hi >> 20) - 896
+        m = (((hi << 3) & 0xFFFFFFFF) | (lo >> 29)) & 0x7FFFFF
+        x2f = 0.0 if e <= 0 else float(np.array([(e << 23) | m], dtype=np.uint32).view(np.float32)[0])
+        t = qf[2]
+        for k in (7, 6):
+            t = np.float32(float(t) * x2f + float(qf[k - 6]))  # fma: exact product, one FP64 rounding
+        T = sum(mpmath.mpf(q[k]) * mpmath.mpf(x2) ** (k - 6) for k in (6, 7, 8))
+        err = abs(mpmath.mpf(xi) * mpmath.mpf(x2) ** 6 * (mpmath.mpf(float(t)) - T))
+        worst = max(worst, float(err))
+    return worst
+
+
+def test_fp64_series_split_error_bound(L):
+    """Wherever the library enables the FP32 tail, its effect on theta stays below 2^-58 for
+    |xi| <= 1 (the clamped range under Theorem 2), the bound the split is admitted by:
+    at the stated workloads' time steps and at the largest time step that still splits."""
+    import numpy as np
+    xs = list(np.linspace(-1.0, 1.0, 801)) + [1.0, -1.0, 0.999999, 2.0 ** -30]
+    for dt in (0.005685895945577131, 0.0017157758860686684):
+        assert _tail_error(dt, xs) <= 2.0 ** -58
+    # the largest dt (series, Theorem 2 holding: 2D with a fine grid) whose context splits
+    lo, hi = 0.001, 0.05
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if _root(L, 2, (64, 64), 0.001, mid, 1 / 64, 1, 1)[1]:
+            lo = mid
+        else:
+            hi = mid
+    assert _root(L, 2, (64, 64), 0.001, lo, 1 / 64, 1, 1) == (1, 1)
+    assert _tail_error(lo, xs) <= 2.0 ** -58
