@@ -184,3 +184,57 @@ def test_temporal_batch_unsupported_and_autotune(acs, tmp_path, monkeypatch):
     b2 = acs.Batch(*args, "f32")
     assert b2.get_config() == cfg and b2.get_temporal() == tcfg
     b2.close()
+
+
+def test_temporal_batch_all_root_modes(acs):
+    """Instances in every root mode the per-unit dispatch selects: the series under
+    Theorem 2's clamp, the series with its run-time range tests (time step above the
+    maximum-principle bound, so no clamp), and the Newton root with and without the clamp.
+    Every depth gives the single-step kernel's bits (NaN-aware, since states beyond the
+    theorems' conditions may grow) and the standalone runs' bits."""
+    import ctypes
+    cases = [(256, 0.03, 0.006, 1 / 256, 1),        # series, no clamp (dt > 1 / (1 + 4 eps^2 / h^2))
+             (200, 0.03, 0.008, 1 / 200, 0),        # series, no clamp
+             (64, 0.02, 0.5, 1 / 64, 2),            # Newton, no clamp
+             (100, 0.02, 0.3, 1 / 101, 2),          # Newton, no clamp
+             (77, 0.01, 0.05, 1 / 77, 1),           # Newton under the clamp
+             (300, 0.03, dt_rule(2, 0.03, 1 / 300), 1 / 300, 0)]  # series under the clamp
+    L = acs.lib()
+    modes = []
+    for n, eps, dt, h, bc in cases:
+        c = ctypes.c_void_p()
+        nn = (ctypes.c_int64 * 3)(n, n, 1)
+        assert L.acs_create(2, nn, eps, dt, h, bc, 0, ctypes.byref(c)) >= 0
+        m = ctypes.c_int()
+        assert L.acs_get_root(c, ctypes.byref(m), None) == 0
+        modes.append(m.value)
+        L.acs_destroy(c)
+    assert modes == [acs.ACS_ROOT_SERIES, acs.ACS_ROOT_SERIES, acs.ACS_ROOT_NEWTON, acs.ACS_ROOT_NEWTON,
+                     acs.ACS_ROOT_NEWTON, acs.ACS_ROOT_SERIES]
+    args = tuple(list(x) for x in zip(*cases))
+    rng = np.random.default_rng(21)
+    phi0 = [rng.uniform(-1, 1, (n, n)).astype(np.float32) for n in args[0]]
+    for steps in (8, 13):
+        ref, _, _ = _run_nan(acs, args, phi0, steps)
+        for depth in (2, 3, 4):
+            got, _, _ = _run_nan(acs, args, phi0, steps, depth, 32, depth % 2)
+            for k in range(len(cases)):
+                assert np.array_equal(got[k], ref[k], equal_nan=True), (steps, depth, k)
+    for k, (n, eps, dt, h, bc) in enumerate(cases):
+        s = acs.AllenCahn((n, n), eps, dt, h, bc, "f32")
+        s.set_state(phi0[k])
+        s.step(13)
+        assert np.array_equal(got[k], s.numpy(), equal_nan=True), k
+        s.close()
+
+
+def _run_nan(acs, args, phi0, steps, depth=1, rows=0, order=0):
+    """_run without the reductions (states beyond the theorems' conditions may not stay
+    finite, which acs_batch_observe reports as an error)."""
+    b = acs.Batch(*args, "f32")
+    b.set_temporal(depth, rows, order)
+    b.set_states(phi0)
+    b.step(steps)
+    out = b.states()
+    b.close()
+    return out, None, None
