@@ -7,6 +7,8 @@ kernel for K = 2, 3, 4, every boundary, both precisions, grids smaller than one 
 partial strips and partial row chunks, step counts that are not multiples of K, and
 against the FP64 oracle (max-abs relative 1e-12).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -183,3 +185,48 @@ def test_temporal_unsupported_shapes(acs):
         with pytest.raises(acs.AcsError) as e:
             s.set_kernel(acs.ACS_KERNEL_TEMPORAL, depth)
         assert e.value.status == acs.ACS_E_UNSUPPORTED
+
+
+# Beyond Theorem 2's step-size condition but within Theorem 3's: the root runs without the
+# clamp -- the series with its run-time range tests, or the Newton root -- and the states
+# stay bounded.  (shape, eps, dt, h, dtype, expected root mode, depths)
+UNCLAMPED = [
+    ((130, 256), math.sqrt(0.248 / 0.01) / 256, 0.01, 1 / 256, "f32", 1, (2, 3, 4)),
+    ((130, 256), math.sqrt(0.2497 / 0.002) / 256, 0.002, 1 / 256, "f64", 1, (2, 4)),
+    ((130, 256), math.sqrt(0.2 / 0.5) / 256, 0.5, 1 / 256, "f32", 0, (2, 3, 4)),
+    ((130, 256), math.sqrt(0.2 / 0.5) / 256, 0.5, 1 / 256, "f64", 0, (3,)),
+    ((20, 70, 130), math.sqrt(0.1658 / 0.01) / 130, 0.01, 1 / 130, "f32", 1, (2,)),
+    ((20, 70, 130), math.sqrt(0.1 / 0.5) / 130, 0.5, 1 / 130, "f32", 0, (2,)),
+]
+
+
+@pytest.mark.parametrize("bc", BCS, ids=lambda b: BCN[b])
+@pytest.mark.parametrize("case", range(len(UNCLAMPED)))
+def test_temporal_unclamped_root_modes(acs, case, bc):
+    """Temporal passes equal single steps bit for bit when the root runs without Theorem
+    2's clamp (acs_get_root confirms the mode; acs_dt_max that dt exceeds the
+    maximum-principle bound but not the energy bound); FP64 also matches the oracle."""
+    import ctypes
+    shape, eps, dt, h, dtype, mode, depths = UNCLAMPED[case]
+    dmp, den = ctypes.c_double(), ctypes.c_double()
+    assert acs.lib().acs_dt_max(len(shape), eps, h, ctypes.byref(dmp), ctypes.byref(den)) == 0
+    assert dmp.value < dt <= den.value
+    phi0 = uniform_field(shape, -1.0, 1.0, 700 + case + bc)
+    b = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+    m = ctypes.c_int()
+    assert acs.lib().acs_get_root(b.ctx, ctypes.byref(m), None) == 0 and m.value == mode
+    b.set_kernel(acs.ACS_KERNEL_NAIVE)
+    b.set_state(phi0)
+    b.step(13)
+    ref = b.numpy()
+    assert np.isfinite(ref).all()
+    if dtype == "f64":
+        assert relerr(ref, oracle.run_fd(phi0, eps, dt, h, bc, 13)) <= 1e-12
+    for depth in depths:
+        a = acs.AllenCahn(shape, eps, dt, h, bc, dtype)
+        a.set_kernel(acs.ACS_KERNEL_TEMPORAL, depth)
+        a.set_state(phi0)
+        a.step(13)
+        assert np.array_equal(a.numpy(), ref), depth
+        a.close()
+    b.close()
