@@ -121,3 +121,46 @@ def test_lines_full_workload(acs):
         s.step(LINE_STEPS)
         assert np.array_equal(got[k], s.numpy()), k
         s.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("mode", ["series", "newton"])
+def test_lines_unclamped_root_modes(acs, dtype, mode):
+    """Every size class with the root unclamped: dt above Theorem 2's bound but within
+    Theorem 3's (lambda = 0.4993 at dt = 0.002, the series with its range tests; lambda =
+    0.4 at dt = 0.5, the Newton root).  Bit-identical to the standalone 1D path; FP64
+    within 1e-12 of the oracle."""
+    import ctypes
+    lam, dt = (0.4993, 0.002) if mode == "series" else (0.4, 0.5)
+    n, eps, dts, h, bc = [], [], [], [], []
+    for m in SIDES:
+        for b in (0, 1, 2):
+            hh = 1.0 / (m + 1) if b == 2 else 1.0 / m
+            n.append(m)
+            h.append(hh)
+            eps.append(float(np.sqrt(lam / dt)) * hh)
+            dts.append(dt)
+            bc.append(b)
+    want = acs.ACS_ROOT_SERIES if mode == "series" else acs.ACS_ROOT_NEWTON
+    for k in range(len(n)):
+        dmp, den = acs.dt_max(1, eps[k], h[k])
+        assert dmp < dt <= den
+    L = acs.Lines(n, eps, dts, h, bc, dtype)
+    nd = np.float32 if dtype == "f32" else np.float64
+    rng = np.random.default_rng(9)
+    phi0 = [rng.uniform(-1, 1, size=m).astype(nd) for m in n]
+    L.set_states(phi0)
+    L.step(17)
+    got = L.states()
+    for k in range(len(n)):
+        s = acs.AllenCahn((n[k],), eps[k], dts[k], h[k], bc[k], dtype)
+        m = ctypes.c_int()
+        assert acs.lib().acs_get_root(s.ctx, ctypes.byref(m), None) == 0 and m.value == want
+        s.set_state(phi0[k])
+        s.step(17)
+        ref = s.numpy()
+        s.close()
+        assert np.isfinite(ref).all() and np.array_equal(got[k], ref), (n[k], bc[k])
+        if dtype == "f64" and k % 5 == 0:
+            o = oracle.run_fd(phi0[k].astype(np.float64), eps[k], dts[k], h[k], bc[k], 17)
+            assert float(np.abs(got[k] - o).max() / max(np.abs(o).max(), 1e-300)) <= 1e-12
