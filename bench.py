@@ -16,8 +16,9 @@ value     lattice updates per second over all ranks (GLUPS), device-timed with C
 e2e       the same metric through the C ABI with host buffers: every step is one job
           that copies phi0 from pinned host memory, runs, and copies the state and the
           reductions back.  Reported: the pipelined runner (acs_pipe_submit / wait),
-          whose copies overlap the neighbouring jobs' compute; serial_value: one
-          context (acs_set_state_host, acs_run_logged, acs_get_state_host).
+          whose copies overlap the neighbouring jobs' compute, timed over max(K, 10)
+          jobs (`jobs`); serial_value: one context (acs_set_state_host, acs_run_logged,
+          acs_get_state_host), K jobs (`serial_jobs`).
 roofline  the step kernel's algorithmic bytes per launch (2 sizeof(T) per update, K
           fused steps per launch for temporal blocking) over its CUDA-event launch
           duration, against the measured HBM copy bandwidth.
